@@ -1,0 +1,347 @@
+"""Benchmark: Heat-2D 5-point Jacobi, 8192 x 8192 interior, T = 512 steps.
+
+One step = one call of the library's run entry point advancing the whole grid
+by T = 512 time steps under the recursive (cache-oblivious) tile schedule in
+FP32 (the paper's hot loop: skewed tile lattice -> recursive queue ->
+persistent executor -> register/shared-memory trapezoid tiles).  Inputs are
+seeded synthetic U[0,1) values with a zero Dirichlet ring (resident in HBM
+before timing; the two 256 MiB buffers exceed the 129 MB L2, so no flush is
+needed between steps).
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (the
+plain FP64 naive sweep) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 8192
+T_STEPS = 512
+HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
+METRIC = "GUpdates/s & DRAM bytes/update vs plain sweep; % HBM roofline at stated error"
+UNIT = "GUpdates/s"
+# Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
+BEST = {"schedule": "cot", "tile": (64, 480), "time_depth": 4, "cot_threshold": (4, 8, 8)}
+WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    valid only while the kernel sources hash to the value recorded there."""
+    path = os.path.join(ROOT, "profiles", "cot_heat2d_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for fn in rec.get("sources", []):
+        with open(os.path.join(ROOT, fn), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sources_sha256") or rec.get("kernel") != kernel_tag:
+        return None
+    return rec.get("bytes_per_launch_full")
+
+
+def _cpu_oracle_sample(seconds=12.0, threads=None):
+    """The oracle (naive FP64 sweep, OpenMP over rows) on the full 8192^2 grid
+    for as many steps as fit in about `seconds`; returns (GU/s, steps, cores)."""
+    import numpy as np
+    import oracle
+    import seeded_inputs as si
+    oracle.build()
+    cores = threads or os.cpu_count() or 1
+    sizes = (N_SIDE, N_SIDE)
+    g = si.uniform_grid(sizes, 2, dtype=np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.sweep(g, sizes, HEAT2D, 1, threads=cores)
+    one = time.perf_counter() - t0
+    steps = max(1, min(64, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.sweep(g, sizes, HEAT2D, steps, threads=cores)
+    dt = time.perf_counter() - t0
+    return N_SIDE * N_SIDE * steps / dt / 1e9, steps, cores
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import seeded_inputs as si
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sizes = (N_SIDE, N_SIDE)
+    g = si.uniform_grid(sizes, 2, dtype=np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.sweep(g, sizes, HEAT2D, 1, threads=cores)
+    one = time.perf_counter() - t0
+    # Each step: a bounded sample (whole grid, a few time steps) sized so the
+    # whole run stays within a couple of minutes.
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample_steps = max(1, min(T_STEPS, int(budget / max(one, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.sweep(g, sizes, HEAT2D, sample_steps, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweep(g, sizes, HEAT2D, sample_steps, threads=cores)
+    dt = time.perf_counter() - t0
+    v = N_SIDE * N_SIDE * sample_steps * args.steps / dt / 1e9
+    sample = f"full 8192^2 grid, {sample_steps} of the {T_STEPS} steps per bench step (FP64 naive sweep)"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1802_00166_gb300 as pcot
+    import seeded_inputs as si
+    from paper_1802_00166_gb300 import build as pbuild
+
+    ws, rank, local = _dist()
+    pbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    sched = pcot.SCHEDULES[args.schedule or BEST["schedule"]]
+    params = pcot.tile_params(tile=BEST["tile"], time_depth=BEST["time_depth"],
+                              cot_threshold=BEST["cot_threshold"])
+    sizes = (N_SIDE, N_SIDE)
+    shape = (N_SIDE + 2, N_SIDE + 2)
+    pitch = ((N_SIDE + 2 + 31) // 32) * 32           # 128-byte rows for 16-byte vector access
+    strides = (pitch, 1)
+    h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+    g0 = si.uniform_grid(sizes, 2, dtype=np.float32)
+    base = torch.zeros(shape[0] * pitch, dtype=torch.float32, device="cuda")
+    view = torch.as_strided(base, shape, strides)
+    view.copy_(torch.from_numpy(g0).cuda())
+    nb = pcot.pcot_workspace_bytes(h, sizes, strides, T_STEPS, pcot.PCOT_F32, sched, params)
+    wsbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+    def step():
+        pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, pcot.PCOT_F32, sched,
+                      params, stream)
+
+    for _ in range(args.warmup):
+        step()
+    st = pcot.pcot_check(h, stream)
+    if st != pcot.PCOT_OK:
+        raise pcot.PcotError(st, "warm-up")
+    n0 = pcot.pcot_launch_count(h)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = pcot.pcot_launch_count(h) - n0
+    st = pcot.pcot_check(h, stream)
+    if st != pcot.PCOT_OK:
+        raise pcot.PcotError(st, "timed region")
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = float(N_SIDE * N_SIDE * T_STEPS)
+    value = updates * args.steps * ws / (ms / 1e3) / 1e9
+
+    # End to end through the host-buffer entry point (pinned host grid, the
+    # H2D copy, the run and the D2H copy inside each timed step).
+    host = torch.empty(shape[0] * pitch, dtype=torch.float32).pin_memory()
+    host.copy_(base.cpu())
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pcot.pcot_run_host(h, host.data_ptr(), base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS,
+                           pcot.PCOT_F32, sched, params, stream)
+    e2e_dt = time.perf_counter() - t0
+    span = (shape[0] - 1) * pitch + shape[1]
+    e2e = {"value": updates * e2e_steps * ws / e2e_dt / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": span * 4, "d2h_bytes_per_step": span * 4}
+
+    # Roofline of the dominant kernel (the persistent executor: one launch per
+    # step).  Algorithmic bytes per launch = time blocks x one read + one write
+    # of the grid (the temporal-blocking model); duration = the step's events.
+    q = pcot.pcot_plan_query(h, sizes, T_STEPS, pcot.PCOT_F32, params, with_queue=False)
+    blocks = q["lattice"][0] if sched == pcot.PCOT_COT else math.ceil(T_STEPS / q["depth"])
+    alg_bytes = blocks * 2.0 * N_SIDE * N_SIDE * 4
+    peak, peak_kind = _peaks()
+    launch_s = ms / 1e3 / args.steps
+    achieved = alg_bytes / launch_s / 1e9
+    kernel_tag = f"cot_kernel f32 k={q['depth']} tile={q['tile_ext'][:2]} theta={list(BEST['cot_threshold'])}"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic_from_profile(kernel_tag), "peak_kind": peak_kind,
+            "kernel": kernel_tag, "alg_bytes_per_launch": alg_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "schedule": args.schedule or BEST["schedule"],
+                       "tile": list(q["tile_ext"][:2]), "time_depth": q["depth"],
+                       "cot_threshold": list(BEST["cot_threshold"]), "l2": "inputs larger than L2 (2 x 256 MiB)",
+                       "parallelism": "replicas" if ws > 1 else "single-gpu"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if rank == 0 and not args.no_cpu_baseline:
+        v, steps, cores = _cpu_oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
+    if args.schedules and rank == 0:
+        line["schedules"] = compare_schedules(pcot, h, base, wsbuf, sizes, strides, stream)
+    pcot.pcot_destroy(h)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def compare_schedules(pcot, h, base, wsbuf, sizes, strides, stream):
+    """Context numbers: sweep / SLT / COT in FP32 and the FP64 modes."""
+    import torch
+    out = {}
+    cases = [("sweep_f32", pcot.PCOT_SWEEP, pcot.PCOT_F32, None),
+             ("slt_f32", pcot.PCOT_SLT, pcot.PCOT_F32, BEST),
+             ("cot_f32", pcot.PCOT_COT, pcot.PCOT_F32, BEST)]
+    for name, sched, dt, p in cases:
+        prm = None if p is None else pcot.tile_params(tile=p["tile"], time_depth=p["time_depth"],
+                                                      cot_threshold=p["cot_threshold"])
+        pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, dt, sched, prm, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, dt, sched, prm, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out[name] = {"ms": ms, "GUpdates/s": N_SIDE * N_SIDE * T_STEPS / ms / 1e6}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--schedule", default=None, choices=[None, "sweep", "slt", "cot"])
+    ap.add_argument("--schedules", action="store_true", help="also time sweep / SLT / COT side by side")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

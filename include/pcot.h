@@ -1,0 +1,210 @@
+/*
+ * pcot.h -- C ABI of the GB300 (sm_103a) engine for time-iterated affine star
+ * stencils under the tile schedules studied in "PCOT: Cache Oblivious Tiling
+ * of Polyhedral Programs" (Ranasinghe, Prajapati, Yuki, Rajopadhye;
+ * arXiv 1802.00166).
+ *
+ * Problem statement (Sec. 3.1, Sec. 4.1, Sec. 4.2): a fully permutable affine
+ * loop nest over a rectangular spatial domain repeated for T time steps.  The
+ * loop body is the star-stencil point update
+ *
+ *     u^{t+1}[x] = c_0 u^t[x] + sum_{axis a} sum_{o in -r..-1, +1..+r} c_{a,o} u^t[x + o e_a]
+ *
+ * (the Jacobi-1D 3-point, Heat-2D 5-point and Jacobi-3D 7-point kernels of
+ * Sec. 5.1.2 and Appendix A), with the two-buffer t%2 storage of the
+ * Appendix A example.  Three schedules compute the identical result:
+ *   PCOT_SWEEP  one pass over the grid per time step (the untiled loop nest);
+ *   PCOT_SLT    single-level tiling: time blocks of depth k executed in
+ *               lexicographic order, spatial tiles of a block concurrently
+ *               (Sec. 3.3, "Single-Level Tiling");
+ *   PCOT_COT    the recursive divide-and-conquer order of Sec. 4 applied to
+ *               the lattice of (time block, spatial tile) leaves after time
+ *               skewing, run by one persistent kernel with dependency counters
+ *               in place of the OpenMP task waits of Sec. 4.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Coefficients: ncoeffs = 1 + 2*dims*radius doubles, ordered centre, then
+ *    axis 0 (slowest) .. axis dims-1 (fastest); per axis offsets -r..-1 then
+ *    +1..+r.  The update accumulates in exactly that order.
+ *  Grid layout: row-major, the last axis contiguous (stride 1).  `sizes` are
+ *    the INTERIOR sizes n_a.  Dirichlet grids store n_a + 2r entries per axis;
+ *    the outer ring of width r holds fixed boundary values that are never
+ *    written.  Periodic grids store n_a entries per axis and wrap.
+ *  Strides: `strides` (element strides per axis, last entry 1) may be NULL for
+ *    the contiguous layout.  A padded pitch whose byte size is a multiple of
+ *    16 (and a 16-byte-aligned base) lets the kernels use 16-byte vector
+ *    accesses; other layouts are accepted and run with narrower accesses.
+ *  Precision: PCOT_F32 grids hold float and may use fused multiply-add;
+ *    PCOT_F64 grids hold double and may use fused multiply-add;
+ *    PCOT_F64_EXACT grids hold double and use separately rounded multiply and
+ *    add in the order above, so results are bitwise identical to a plain
+ *    IEEE-754 binary64 evaluation of the definition.
+ *  Memory: every `grid` / `workspace` pointer is DEVICE memory owned by the
+ *    caller unless a parameter says "host".  The handle owns only host-side
+ *    plan caches and a small device status block allocated by pcot_create.
+ *  Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Compute entry points are asynchronous: argument and
+ *    launch errors are returned immediately, device-side errors (a dependency
+ *    wait that timed out, an index outside a buffer) are reported by
+ *    pcot_check.
+ *  Errors: every entry point returns a pcot_status; nothing throws or aborts
+ *    across the ABI.  A handle must not be used from two host threads at once.
+ */
+#ifndef PCOT_H
+#define PCOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PCOT_OK = 0,
+    PCOT_ERR_INVALID_ARG = 1,  /* NULL pointer, size < 1, wrong coefficient count, T < 0 ... */
+    PCOT_ERR_UNSUPPORTED = 2,  /* dims / radius / tile shape this build has no kernel for     */
+    PCOT_ERR_ALIGNMENT = 3,    /* pointer or stride not aligned to the element size          */
+    PCOT_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed                */
+    PCOT_ERR_OOM = 5,          /* workspace too small, or a host allocation failed           */
+    PCOT_ERR_TIMEOUT = 6,      /* a device-side dependency wait gave up (see pcot_check)     */
+    PCOT_ERR_BOUNDS = 7        /* a device-side index check failed (see pcot_check)          */
+} pcot_status;
+
+typedef enum { PCOT_DIRICHLET = 0, PCOT_PERIODIC = 1 } pcot_boundary;
+typedef enum { PCOT_F32 = 0, PCOT_F64 = 1, PCOT_F64_EXACT = 2 } pcot_dtype;
+typedef enum { PCOT_SWEEP = 0, PCOT_SLT = 1, PCOT_COT = 2, PCOT_AUTO = 3 } pcot_schedule;
+
+/*
+ * Tile parameters (Sec. 3.3 "Tile Size": the tile size doubles as the
+ * recursion's leaf size; Sec. 4.5 padding).
+ *  tile[a]          output extent of a spatial tile along axis a (axis 0
+ *                   slowest).  0 picks the default.  The kernels may round an
+ *                   extent (the fastest axis to whole warps); pcot_plan_query
+ *                   reports the extents actually used.
+ *  time_depth       k, the number of time steps a tile advances in one pass
+ *                   (the height of the trapezoid); 0 picks the default.
+ *  cot_threshold[0] leaf orthant extent of the tile lattice in time blocks,
+ *  cot_threshold[1+a]  ... and in tiles along axis a (the recursion's base-case
+ *                   threshold, Sec. 4.2).  0 means 1.
+ */
+typedef struct {
+    int32_t tile[3];
+    int32_t time_depth;
+    int32_t cot_threshold[4];
+} pcot_tile_params;
+
+typedef struct pcot_plan *pcot_handle;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *pcot_status_string(pcot_status s);
+
+/*
+ * Create a stencil handle.
+ *  dims in {1,2,3}; radius must be 1 (the star stencils of Sec. 5.1.2);
+ *  coeffs: ncoeffs = 1 + 2*dims*radius doubles (copied); boundary: Dirichlet
+ *  ring or periodic wrap.  On success *out must be released with
+ *  pcot_destroy.  Device resources of the handle (a small status block and a
+ *  grid-sum partial buffer) are allocated on the current device by the first
+ *  call that launches work; planning calls (pcot_plan_query) need no GPU.
+ */
+pcot_status pcot_create(int dims, int radius, const double *coeffs, int ncoeffs,
+                        pcot_boundary boundary, pcot_handle *out);
+
+/* Release a handle (waits for nothing: call after the last run completed). */
+pcot_status pcot_destroy(pcot_handle h);
+
+/*
+ * Device workspace needed by pcot_run for this problem, step count and
+ * schedule, in bytes (a twin of the grid with the same strides, plus the
+ * per-run dependency counters and tile queue of PCOT_COT, which grow with the
+ * number of time blocks).  `params` may be NULL (defaults).
+ */
+pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t *sizes, const int64_t *strides,
+                                 int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                                 const pcot_tile_params *params, size_t *bytes);
+
+/*
+ * Advance `grid` by T time steps (Sec. 4.2: the result of the original loop
+ * nest, whatever the schedule).
+ *  grid       device, in/out, layout as above; the result is in `grid` for
+ *             every T (the library arranges an even number of buffer swaps).
+ *  workspace  device scratch of at least pcot_workspace_bytes bytes, 256-byte
+ *             aligned; its contents on entry are ignored and on exit are
+ *             undefined.  The Dirichlet ring is copied into it by the call.
+ *  T          number of time steps, T >= 0; T = 0 returns PCOT_OK at once.
+ *  schedule   PCOT_AUTO picks with the built-in defaults.
+ *  params     NULL = defaults.
+ * Asynchronous on `stream`; call pcot_check to surface device errors.
+ */
+pcot_status pcot_run(pcot_handle h, void *grid, void *workspace, const int64_t *sizes,
+                     const int64_t *strides, int64_t T, pcot_dtype dtype,
+                     pcot_schedule schedule, const pcot_tile_params *params, void *stream);
+
+/*
+ * End-to-end variant of pcot_run for host-resident data: copies `host_grid`
+ * (host memory, pinned for best speed, same layout) to `dev_grid`, runs
+ * pcot_run, copies the result back into `host_grid`, and synchronises the
+ * stream before returning (so it also reports device errors like pcot_check).
+ */
+pcot_status pcot_run_host(pcot_handle h, void *host_grid, void *dev_grid, void *workspace,
+                          const int64_t *sizes, const int64_t *strides, int64_t T,
+                          pcot_dtype dtype, pcot_schedule schedule,
+                          const pcot_tile_params *params, void *stream);
+
+/*
+ * Synchronise `stream` and read the handle's device status block: returns
+ * PCOT_OK, PCOT_ERR_TIMEOUT (a dependency wait of the persistent executor
+ * exceeded its limit; the kernel returned without hanging) or PCOT_ERR_BOUNDS,
+ * and clears the block.  CUDA errors of the stream map to PCOT_ERR_CUDA.
+ */
+pcot_status pcot_check(pcot_handle h, void *stream);
+
+/*
+ * Describe the PCOT_COT plan for a problem (for inspection and the legality
+ * tests).  Writes lattice[0] = number of time blocks run by the persistent
+ * kernel, lattice[1+a] = tiles along axis a; tile_ext[a] = tile output extent
+ * used; *depth = time steps per block; *n_tiles = number of queue entries.
+ * If `queue` is non-NULL it receives n_tiles entries (capacity `cap`) in
+ * execution order, each the linear lattice index
+ * ((b * L_0 + i_0) * L_1 + i_1) * L_2 + i_2; `deps` (may be NULL) receives the
+ * initial dependency count of each entry of `queue`.  `tail_steps` receives
+ * the steps run after the persistent kernel by single-level launches.
+ */
+pcot_status pcot_plan_query(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
+                            const pcot_tile_params *params, int32_t *lattice, int32_t *tile_ext,
+                            int32_t *depth, int64_t *n_tiles, int64_t *tail_steps,
+                            int32_t *queue, int32_t *deps, int64_t cap);
+
+/*
+ * Test hook: the persistent executor's dependency wait with a counter that
+ * nothing releases.  Launches one CTA that waits on a count of 1 with a limit
+ * of `timeout_ms` milliseconds; the kernel records PCOT_ERR_TIMEOUT in the
+ * status block and returns.  pcot_check then returns PCOT_ERR_TIMEOUT.
+ */
+pcot_status pcot_test_wait_timeout(pcot_handle h, void *workspace, int32_t timeout_ms, void *stream);
+
+/*
+ * Conservation check (sum of the interior): *out_device (device, one double)
+ * receives the FP64 sum of all interior values of `grid` (float grids are
+ * widened before adding).  The reduction order is fixed by the problem size,
+ * so repeated calls give bitwise identical sums.  Uses a partial-sum buffer
+ * owned by the handle (allocated by pcot_create).
+ */
+pcot_status pcot_grid_sum(pcot_handle h, const void *grid, const int64_t *sizes,
+                          const int64_t *strides, pcot_dtype dtype, double *out_device,
+                          void *stream);
+
+/*
+ * Number of kernels this handle has launched since it was created (sweep
+ * steps, single-level blocks, persistent executors, ring copies, sums).
+ * Host-side counter; lets a caller state how many of its GPU launches were
+ * the library's.
+ */
+pcot_status pcot_launch_count(pcot_handle h, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCOT_H */

@@ -67,6 +67,9 @@ def _load():
             lib.oracle_orthant_empty.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64,
                                                  _I64P, _I64P]
             lib.oracle_orthant_empty.restype = ctypes.c_int
+            lib.oracle_pcot_order.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64, _I64P,
+                                              _I64P, ctypes.c_int64]
+            lib.oracle_pcot_order.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -127,6 +130,21 @@ def pcot(grid, sizes, coeffs, T, leaf, radius=1, return_stats=False):
         keys = ("recursive_calls", "base_calls", "zero_exits", "empty_exits", "points", "max_depth")
         return g, dict(zip(keys, (int(v) for v in stats)))
     return g
+
+
+def pcot_order(sizes, T, leaf, radius=1):
+    """Points (t, i_0, ..) in the order the recursion's base function visits
+    them (Sec. 4.2-4.5), as an (npoints, dims+1) int64 array."""
+    sizes = _i64(sizes)
+    leaf = _i64(leaf)
+    d = len(sizes)
+    lib = _load()
+    npts = lib.oracle_pcot_order(d, radius, _ptr(sizes, _I64P), int(T), _ptr(leaf, _I64P), None, 0)
+    if npts < 0:
+        raise RuntimeError("oracle_pcot_order failed")
+    out = np.zeros((max(npts, 1), d + 1), dtype=np.int64)
+    lib.oracle_pcot_order(d, radius, _ptr(sizes, _I64P), int(T), _ptr(leaf, _I64P), _ptr(out, _I64P), int(npts))
+    return out[:npts]
 
 
 def padded_box(sizes, T, leaf, radius=1):

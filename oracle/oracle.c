@@ -166,6 +166,8 @@ typedef struct {
     int64_t leaf[OR_MAXD + 1];
     double *X[2];
     int64_t stats[6];        /* recursive calls, base calls, zero exits, empty exits, points, max depth */
+    int64_t *record;         /* when set: base loops record (t, i_0..i_{d-1}) instead of computing */
+    int64_t record_cap;
 } or_pcot;
 
 /* Bounding box of D (Sec. 4.5): eliminating t from r t <= x'_a <= r t + n_a - 1
@@ -240,6 +242,8 @@ static void or_base(or_pcot *p, const int64_t *lo, const int64_t *size)
         if (!any) continue;
         const double *src = p->X[(t - 1) % 2];
         double *dst = p->X[t % 2];
+        (void)src;
+        (void)dst;
         int64_t x[OR_MAXD];
         for (int a = 0; a < g->dims; ++a) x[a] = xl[a];
         for (;;) {
@@ -249,7 +253,15 @@ static void or_base(or_pcot *p, const int64_t *lo, const int64_t *size)
                 i[a] = x[a] - g->r * t;
                 s += (i[a] + g->r) * g->stride[a];
             }
-            dst[s] = or_point(g, i, src);
+            if (p->record) {
+                int64_t k = p->stats[4];
+                if (k < p->record_cap) {
+                    p->record[k * (g->dims + 1)] = t;
+                    for (int a = 0; a < g->dims; ++a) p->record[k * (g->dims + 1) + 1 + a] = i[a];
+                }
+            } else {
+                dst[s] = or_point(g, i, src);
+            }
             p->stats[4]++;
             int a = g->dims - 1;
             while (a >= 0) {
@@ -364,4 +376,36 @@ int oracle_orthant_empty(int dims, int r, const int64_t *n, int64_t T,
     memset(cdummy, 0, sizeof(cdummy));
     if (r > 8 || or_setup(&g, dims, r, n, 0, cdummy) != 0) return -1;
     return or_check_empty(&g, T, lo, size);
+}
+
+/*
+ * Visit order of the recursion: the points (t, i_0..i_{d-1}) in the order the
+ * base function reaches them (same recursion as oracle_pcot, nothing computed).
+ * `out` receives up to `cap` records of dims+1 int64 each; returns the number
+ * of points of the domain (which may exceed cap), or -1 on bad arguments.
+ */
+int64_t oracle_pcot_order(int dims, int r, const int64_t *n, int64_t T, const int64_t *leaf,
+                          int64_t *out, int64_t cap)
+{
+    or_pcot p;
+    double cdummy[1 + 2 * OR_MAXD * 8];
+    memset(&p, 0, sizeof(p));
+    memset(cdummy, 0, sizeof(cdummy));
+    if (r > 8 || or_setup(&p.g, dims, r, n, 0, cdummy) != 0 || T < 0 || !leaf) return -1;
+    p.D = dims + 1;
+    p.T = T;
+    for (int i = 0; i < p.D; ++i) {
+        if (leaf[i] < 1) return -1;
+        p.leaf[i] = leaf[i];
+    }
+    p.record = out;
+    p.record_cap = out ? cap : 0;
+    if (!out) { static int64_t sink[OR_MAXD + 1]; p.record = sink; p.record_cap = 0; }
+    if (T > 0) {
+        int64_t lo[OR_MAXD + 1], size[OR_MAXD + 1];
+        or_bbox(&p.g, T, lo, size);
+        for (int i = 0; i < p.D; ++i) size[i] = or_pad(size[i], p.leaf[i], NULL);
+        or_recurse(&p, lo, size, 0);
+    }
+    return p.stats[4];
 }

@@ -1,0 +1,240 @@
+"""Python binding of libpcot.so (the GB300 stencil engine's C ABI).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name in ``include/pcot.h``; every step of the computation runs in the
+library's CUDA kernels.  PyTorch is used for device memory and streams.  The
+library must have been built (``python -m paper_1802_00166_gb300.build``);
+importing this module without it raises, there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcot.so")
+
+PCOT_OK = 0
+PCOT_ERR_INVALID_ARG = 1
+PCOT_ERR_UNSUPPORTED = 2
+PCOT_ERR_ALIGNMENT = 3
+PCOT_ERR_CUDA = 4
+PCOT_ERR_OOM = 5
+PCOT_ERR_TIMEOUT = 6
+PCOT_ERR_BOUNDS = 7
+
+PCOT_DIRICHLET = 0
+PCOT_PERIODIC = 1
+
+PCOT_F32 = 0
+PCOT_F64 = 1
+PCOT_F64_EXACT = 2
+
+PCOT_SWEEP = 0
+PCOT_SLT = 1
+PCOT_COT = 2
+PCOT_AUTO = 3
+
+SCHEDULES = {"sweep": PCOT_SWEEP, "slt": PCOT_SLT, "cot": PCOT_COT, "auto": PCOT_AUTO}
+DTYPES = {"f32": PCOT_F32, "f64": PCOT_F64, "f64_exact": PCOT_F64_EXACT}
+
+
+class PcotError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class pcot_tile_params(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32 * 3), ("time_depth", ctypes.c_int32),
+                ("cot_threshold", ctypes.c_int32 * 4)]
+
+
+def tile_params(tile=(0, 0, 0), time_depth=0, cot_threshold=(0, 0, 0, 0)):
+    p = pcot_tile_params()
+    for i, v in enumerate(list(tile)[:3]):
+        p.tile[i] = int(v)
+    p.time_depth = int(time_depth)
+    for i, v in enumerate(list(cot_threshold)[:4]):
+        p.cot_threshold[i] = int(v)
+    return p
+
+
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_VP = ctypes.c_void_p
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1802_00166_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    S = ctypes.c_int
+    sig = {
+        "pcot_status_string": (ctypes.c_char_p, [S]),
+        "pcot_create": (S, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                            ctypes.c_int, ctypes.POINTER(_VP)]),
+        "pcot_destroy": (S, [_VP]),
+        "pcot_workspace_bytes": (S, [_VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_run": (S, [_VP, _VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                         ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_run_host": (S, [_VP, _VP, _VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_check": (S, [_VP, _VP]),
+        "pcot_plan_query": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
+                                _I32P, _I32P, _I32P, _I64P, _I64P, _I32P, _I32P, ctypes.c_int64]),
+        "pcot_test_wait_timeout": (S, [_VP, _VP, ctypes.c_int32, _VP]),
+        "pcot_grid_sum": (S, [_VP, _VP, _I64P, _I64P, ctypes.c_int, _VP, _VP]),
+        "pcot_launch_count": (S, [_VP, _I64P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared in include/pcot.h that this binding marshals."""
+    return ["pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
+            "pcot_run_host", "pcot_check", "pcot_plan_query", "pcot_test_wait_timeout", "pcot_grid_sum",
+            "pcot_launch_count"]
+
+
+def status_string(s):
+    return _load().pcot_status_string(int(s)).decode()
+
+
+def _chk(st, where):
+    if st != PCOT_OK:
+        raise PcotError(st, where)
+
+
+def _i64(v):
+    if v is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+    return a
+
+
+def _p64(a):
+    return None if a is None else a.ctypes.data_as(_I64P)
+
+
+def _ptr(t):
+    """Device/host address of a tensor, array or integer."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _params(p):
+    if p is None:
+        return None
+    if isinstance(p, pcot_tile_params):
+        return ctypes.byref(p)
+    if isinstance(p, dict):
+        return ctypes.byref(tile_params(**p))
+    raise TypeError("params must be pcot_tile_params, a dict or None")
+
+
+def pcot_create(dims, radius, coeffs, boundary):
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    h = _VP()
+    _chk(_load().pcot_create(int(dims), int(radius), c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             int(c.size), int(boundary), ctypes.byref(h)), "pcot_create")
+    return h
+
+
+def pcot_destroy(h):
+    _chk(_load().pcot_destroy(h), "pcot_destroy")
+
+
+def pcot_workspace_bytes(h, sizes, strides, T, dtype, schedule, params=None):
+    n = ctypes.c_size_t()
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_workspace_bytes(h, _p64(s), _p64(st), int(T), int(dtype), int(schedule), _params(params),
+                                      ctypes.byref(n)), "pcot_workspace_bytes")
+    return int(n.value)
+
+
+def pcot_run(h, grid, workspace, sizes, strides, T, dtype, schedule, params=None, stream=None):
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_run(h, _ptr(grid), _ptr(workspace), _p64(s), _p64(st), int(T), int(dtype), int(schedule),
+                          _params(params), _stream(stream)), "pcot_run")
+
+
+def pcot_run_host(h, host_grid, dev_grid, workspace, sizes, strides, T, dtype, schedule, params=None, stream=None):
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_run_host(h, _ptr(host_grid), _ptr(dev_grid), _ptr(workspace), _p64(s), _p64(st), int(T),
+                               int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_run_host")
+
+
+def pcot_check(h, stream=None):
+    """Returns the status code (does not raise) so tests can inspect it."""
+    return int(_load().pcot_check(h, _stream(stream)))
+
+
+def pcot_plan_query(h, sizes, T, dtype, params=None, with_queue=True):
+    s = _i64(sizes)
+    lat = (ctypes.c_int32 * 4)()
+    ext = (ctypes.c_int32 * 3)()
+    depth = ctypes.c_int32()
+    nt = ctypes.c_int64()
+    tail = ctypes.c_int64()
+    lib = _load()
+    _chk(lib.pcot_plan_query(h, _p64(s), int(T), int(dtype), _params(params), lat, ext, ctypes.byref(depth),
+                             ctypes.byref(nt), ctypes.byref(tail), None, None, 0), "pcot_plan_query")
+    out = dict(lattice=list(lat), tile_ext=list(ext), depth=depth.value, n_tiles=nt.value, tail_steps=tail.value)
+    if with_queue and nt.value > 0:
+        q = np.zeros(nt.value, dtype=np.int32)
+        d = np.zeros(nt.value, dtype=np.int32)
+        _chk(lib.pcot_plan_query(h, _p64(s), int(T), int(dtype), _params(params), None, None, None, None, None,
+                                 q.ctypes.data_as(_I32P), d.ctypes.data_as(_I32P), int(nt.value)), "pcot_plan_query")
+        out["queue"] = q
+        out["deps"] = d
+    return out
+
+
+def pcot_test_wait_timeout(h, workspace, timeout_ms, stream=None):
+    _chk(_load().pcot_test_wait_timeout(h, _ptr(workspace), int(timeout_ms), _stream(stream)),
+         "pcot_test_wait_timeout")
+
+
+def pcot_grid_sum(h, grid, sizes, strides, dtype, out_device, stream=None):
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_grid_sum(h, _ptr(grid), _p64(s), _p64(st), int(dtype), _ptr(out_device), _stream(stream)),
+         "pcot_grid_sum")
+
+
+def pcot_launch_count(h):
+    n = ctypes.c_int64()
+    _chk(_load().pcot_launch_count(h, ctypes.byref(n)), "pcot_launch_count")
+    return int(n.value)
+
+
+def library_path():
+    return LIB_PATH

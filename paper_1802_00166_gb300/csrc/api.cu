@@ -1,0 +1,483 @@
+// C ABI of the stencil engine: argument checks, workspace layout, schedule
+// execution (sweep / single-level / recursive persistent), status block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pcot.h"
+#include "planner.h"
+
+using namespace pcot;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s per dependency wait
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct CotPlanHost {
+    TileGeo tg{};
+    int k = 0;
+    int P = 0;                 // blocks run by the persistent kernel
+    int32_t lattice[4] = {0, 1, 1, 1};
+    int64_t ntiles = 0;
+    BlockPlan tail;            // blocks run afterwards by single-level launches
+    std::vector<int32_t> queue, counts;
+    void* pinned = nullptr;    // upload image: [head block][counts][queue]
+    size_t image_bytes = 0;
+};
+
+}  // namespace
+
+struct pcot_plan {
+    int dims = 0, radius = 1;
+    int boundary = 0;
+    double coeffs[7] = {0, 0, 0, 0, 0, 0, 0};
+    int device = 0;
+    int num_sms = 0;
+    DevStatus* d_status = nullptr;
+    double* d_partials = nullptr;  // grid-sum partials
+    std::map<std::string, CotPlanHost*> cot_cache;
+    uint64_t timeout_ns = kDefaultTimeoutNs;
+    int64_t launches = 0;  // kernels launched by this handle
+};
+
+namespace {
+
+pcot_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PCOT_OK;
+    if (e == cudaErrorMemoryAllocation) return PCOT_ERR_OOM;
+    return PCOT_ERR_CUDA;
+}
+
+#define PCOT_TRY(expr)                         \
+    do {                                       \
+        pcot_status _s = (expr);               \
+        if (_s != PCOT_OK) return _s;          \
+    } while (0)
+
+#define PCOT_CUDA(expr)                        \
+    do {                                       \
+        cudaError_t _e = (expr);               \
+        if (_e != cudaSuccess) return from_cuda(_e); \
+    } while (0)
+
+int elem_size(pcot_dtype dt) { return dt == PCOT_F32 ? 4 : 8; }
+
+// Device resources of a handle, created on first use on the current device.
+pcot_status ensure_device(pcot_handle h) {
+    if (h->d_status) return PCOT_OK;
+    PCOT_CUDA(cudaGetDevice(&h->device));
+    PCOT_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    DevStatus* st = nullptr;
+    double* part = nullptr;
+    cudaError_t e = cudaMalloc((void**)&st, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&part, sizeof(double) * grid_sum_partials());
+    if (e != cudaSuccess) {
+        if (st) cudaFree(st);
+        if (part) cudaFree(part);
+        return from_cuda(e);
+    }
+    h->d_status = st;
+    h->d_partials = part;
+    return PCOT_OK;
+}
+
+// Pinned upload image of a plan, built on first use.
+pcot_status ensure_image(CotPlanHost* c) {
+    if (c->pinned || c->ntiles == 0) return PCOT_OK;
+    void* p = nullptr;
+    PCOT_CUDA(cudaMallocHost(&p, c->image_bytes));
+    unsigned char* img = (unsigned char*)p;
+    const size_t cb = (size_t)c->ntiles * 4;
+    std::memset(img, 0, c->image_bytes);
+    std::memcpy(img + kAlign, c->counts.data(), cb);
+    std::memcpy(img + kAlign + round_up(cb, kAlign), c->queue.data(), cb);
+    c->pinned = p;
+    return PCOT_OK;
+}
+
+pcot_status make_ctx(pcot_handle h, const int64_t* sizes, const int64_t* strides, pcot_dtype dtype,
+                     void* stream, LaunchCtx* L) {
+    if (!h || !sizes) return PCOT_ERR_INVALID_ARG;
+    if (dtype != PCOT_F32 && dtype != PCOT_F64 && dtype != PCOT_F64_EXACT) return PCOT_ERR_INVALID_ARG;
+    std::memset(L, 0, sizeof(*L));
+    L->dtype = (int)dtype;
+    L->stream = (cudaStream_t)stream;
+    DevGeo& g = L->geo;
+    g.dims = h->dims;
+    g.periodic = h->boundary == PCOT_PERIODIC;
+    for (int a = 0; a < kMaxDims; ++a) {
+        g.e[a] = 1;
+        g.n[a] = 1;
+        g.s[a] = 0;
+    }
+    for (int a = 0; a < h->dims; ++a) {
+        if (sizes[a] < 1 || sizes[a] > (int64_t)1 << 40) return PCOT_ERR_INVALID_ARG;
+        if (g.periodic && sizes[a] < 3) return PCOT_ERR_UNSUPPORTED;
+        g.n[a] = sizes[a];
+        g.e[a] = g.periodic ? sizes[a] : sizes[a] + 2 * h->radius;
+    }
+    int64_t s = 1;
+    for (int a = h->dims - 1; a >= 0; --a) {
+        if (strides) {
+            if (a == h->dims - 1 && strides[a] != 1) return PCOT_ERR_UNSUPPORTED;
+            if (strides[a] < s) return PCOT_ERR_INVALID_ARG;  // rows may not overlap
+            g.s[a] = strides[a];
+        } else {
+            g.s[a] = s;
+        }
+        s = g.s[a] * g.e[a];
+    }
+    for (int i = 0; i < 7; ++i) L->coeffs[i] = h->coeffs[i];
+    return PCOT_OK;
+}
+
+size_t span_bytes(const LaunchCtx& L) {
+    int64_t last = 0;
+    for (int a = 0; a < L.geo.dims; ++a) last += (L.geo.e[a] - 1) * L.geo.s[a];
+    return (size_t)(last + 1) * dtype_size(L.dtype);
+}
+
+int default_depth(const LaunchCtx& L) {
+    if (L.geo.dims == 1) return 16;
+    if (L.dtype != kF32) return 1;
+    return L.geo.dims == 2 ? 4 : 2;
+}
+
+std::string plan_key(const LaunchCtx& L, int64_t T, const pcot_tile_params* p) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%d|%d|%lld,%lld,%lld|%lld|%d,%d,%d|%d|%d,%d,%d,%d", L.dtype, L.geo.dims,
+                  (long long)L.geo.n[0], (long long)L.geo.n[1], (long long)L.geo.n[2], (long long)T,
+                  p ? p->tile[0] : 0, p ? p->tile[1] : 0, p ? p->tile[2] : 0, p ? p->time_depth : 0,
+                  p ? p->cot_threshold[0] : 0, p ? p->cot_threshold[1] : 0, p ? p->cot_threshold[2] : 0,
+                  p ? p->cot_threshold[3] : 0);
+    return buf;
+}
+
+std::vector<int> family_depths(int family, int dtype) {
+    int d[32];
+    const int n = supported_depths(family, dtype, d, 32);
+    return std::vector<int>(d, d + n);
+}
+
+// Build (or fetch) the persistent-executor plan of a problem.
+pcot_status get_cot_plan(pcot_handle h, const LaunchCtx& L, int64_t T, const pcot_tile_params* p,
+                         CotPlanHost** out) {
+    const std::string key = plan_key(L, T, p);
+    auto it = h->cot_cache.find(key);
+    if (it != h->cot_cache.end()) {
+        *out = it->second;
+        return PCOT_OK;
+    }
+    if (L.geo.periodic) return PCOT_ERR_UNSUPPORTED;  // the skewed lattice needs a non-wrapping domain
+    int k = p && p->time_depth > 0 ? p->time_depth : default_depth(L);
+    TileGeo tg;
+    if (!choose_tiles(L, p ? p->tile : nullptr, k, &tg)) {
+        // Depth not compiled for the fast family: fall back to its nearest.
+        std::vector<int> ds = family_depths(L.geo.dims == 2 ? kFamStream2D : kFamStream3D, L.dtype);
+        int best = 1;
+        for (int d : ds)
+            if (d <= k) best = d;
+        k = best;
+        if (!choose_tiles(L, p ? p->tile : nullptr, k, &tg)) return PCOT_ERR_UNSUPPORTED;
+    }
+    CotPlanHost* c = new CotPlanHost();
+    c->tg = tg;
+    c->k = k;
+    int64_t P = T / k;
+    if (P % 2 == 1) P -= 1;
+    if (P > (int64_t)1 << 20) {
+        delete c;
+        return PCOT_ERR_UNSUPPORTED;
+    }
+    c->P = (int)P;
+    const int d = L.geo.dims;
+    int64_t Lax[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) Lax[a] = tg.count[a];
+    int64_t total = P * Lax[0] * Lax[1] * Lax[2];
+    if (total > 0x7fffffffLL) {
+        delete c;
+        return PCOT_ERR_UNSUPPORTED;
+    }
+    c->lattice[0] = (int32_t)P;
+    for (int a = 0; a < 3; ++a) c->lattice[1 + a] = (int32_t)Lax[a];
+    c->ntiles = total;
+    int64_t theta[4] = {1, 1, 1, 1};
+    for (int i = 0; i <= d; ++i) theta[i] = p && p->cot_threshold[i] > 0 ? p->cot_threshold[i] : 1;
+    if (P > 0) {
+        c->queue = pcot_lattice_order((int)P, d, Lax, theta, nullptr);
+        c->counts = lattice_dep_counts((int)P, d, Lax);
+        if ((int64_t)c->queue.size() != total) {
+            delete c;
+            return PCOT_ERR_UNSUPPORTED;
+        }
+    }
+    // Remaining steps: single-level blocks with an even count.
+    const int64_t rest = T - P * k;
+    std::vector<int> ds = tg.family == kFamGeneric ? std::vector<int>() : family_depths(tg.family, L.dtype);
+    c->tail = plan_blocks(rest, k, ds);
+    c->image_bytes = kAlign + round_up((size_t)total * 4, kAlign) + round_up((size_t)total * 4, kAlign);
+    h->cot_cache[key] = c;
+    *out = c;
+    return PCOT_OK;
+}
+
+size_t twin_bytes(const LaunchCtx& L) { return round_up(span_bytes(L), kAlign); }
+
+pcot_status run_blocks(pcot_handle h, const LaunchCtx& L, const pcot_tile_params* p, const BlockPlan& bp, void*& cur,
+                       void*& other) {
+    for (int d : bp.depths) {
+        TileGeo tg;
+        if (!choose_tiles(L, p ? p->tile : nullptr, d, &tg)) return PCOT_ERR_UNSUPPORTED;
+        PCOT_CUDA(launch_slt_block(L, tg, cur, other));
+        ++h->launches;
+        std::swap(cur, other);
+    }
+    if (bp.final_copy) {
+        PCOT_CUDA(cudaMemcpyAsync(other, cur, span_bytes(L), cudaMemcpyDeviceToDevice, L.stream));
+        std::swap(cur, other);
+    }
+    return PCOT_OK;
+}
+
+pcot_status run_impl(pcot_handle h, void* grid, void* workspace, const int64_t* sizes, const int64_t* strides,
+                     int64_t T, pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
+                     void* stream) {
+    if (!h || !grid || !workspace || !sizes) return PCOT_ERR_INVALID_ARG;
+    if (T < 0) return PCOT_ERR_INVALID_ARG;
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, strides, dtype, stream, &L));
+    if (((uintptr_t)grid % elem_size(dtype)) != 0) return PCOT_ERR_ALIGNMENT;
+    if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
+    if (schedule < PCOT_SWEEP || schedule > PCOT_AUTO) return PCOT_ERR_INVALID_ARG;
+    if (T == 0) return PCOT_OK;
+    PCOT_TRY(ensure_device(h));
+    if (schedule == PCOT_AUTO) schedule = (L.dtype == kF32 || L.geo.dims == 1) ? PCOT_SLT : PCOT_SWEEP;
+    if (schedule == PCOT_COT && L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
+    void* twin = workspace;
+    if (!L.geo.periodic) {
+        PCOT_CUDA(launch_ring_copy(L, grid, twin));
+        ++h->launches;
+    }
+    void* cur = grid;
+    void* other = twin;
+    if (schedule == PCOT_SWEEP) {
+        for (int64_t t = 0; t < T; ++t) {
+            PCOT_CUDA(launch_sweep(L, cur, other));
+            ++h->launches;
+            std::swap(cur, other);
+        }
+        if (cur != grid) {
+            PCOT_CUDA(cudaMemcpyAsync(grid, cur, span_bytes(L), cudaMemcpyDeviceToDevice, L.stream));
+        }
+        return PCOT_OK;
+    }
+    if (schedule == PCOT_SLT) {
+        int k = params && params->time_depth > 0 ? params->time_depth : default_depth(L);
+        TileGeo probe;
+        std::vector<int> ds;
+        if (choose_tiles(L, params ? params->tile : nullptr, k, &probe)) {
+            ds = probe.family == kFamGeneric ? std::vector<int>() : family_depths(probe.family, L.dtype);
+        } else {
+            const int fam = L.geo.dims == 2 ? kFamStream2D : kFamStream3D;
+            ds = family_depths(fam, L.dtype);
+        }
+        BlockPlan bp = plan_blocks(T, k, ds);
+        PCOT_TRY(run_blocks(h, L, params, bp, cur, other));
+        if (cur != grid) return PCOT_ERR_UNSUPPORTED;  // plan_blocks guarantees an even swap count
+        return PCOT_OK;
+    }
+    // PCOT_COT
+    CotPlanHost* c = nullptr;
+    PCOT_TRY(get_cot_plan(h, L, T, params, &c));
+    if (c->ntiles > 0) {
+        PCOT_TRY(ensure_image(c));
+        unsigned char* ws = (unsigned char*)workspace + twin_bytes(L);
+        PCOT_CUDA(cudaMemcpyAsync(ws, c->pinned, c->image_bytes, cudaMemcpyHostToDevice, L.stream));
+        CotDev q;
+        q.head = (int32_t*)ws;
+        q.counts = (int32_t*)(ws + kAlign);
+        q.queue = (const int32_t*)(ws + kAlign + round_up((size_t)c->ntiles * 4, kAlign));
+        q.ntiles = c->ntiles;
+        for (int i = 0; i < 4; ++i) q.lattice[i] = c->lattice[i];
+        q.status = h->d_status;
+        q.timeout_ns = h->timeout_ns;
+        int per_sm = cot_ctas_per_sm(L, c->tg);
+        int64_t nctas = (int64_t)per_sm * h->num_sms;
+        if (nctas > c->ntiles) nctas = c->ntiles;
+        if (nctas < 1) nctas = 1;
+        PCOT_CUDA(launch_cot(L, c->tg, grid, twin, q, (int)nctas));
+        ++h->launches;
+        // c->P is even: the result of the persistent part is back in grid.
+    }
+    PCOT_TRY(run_blocks(h, L, params, c->tail, cur, other));
+    if (cur != grid) return PCOT_ERR_UNSUPPORTED;
+    return PCOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pcot_status_string(pcot_status s) {
+    switch (s) {
+        case PCOT_OK: return "ok";
+        case PCOT_ERR_INVALID_ARG: return "invalid argument";
+        case PCOT_ERR_UNSUPPORTED: return "unsupported";
+        case PCOT_ERR_ALIGNMENT: return "misaligned pointer or stride";
+        case PCOT_ERR_CUDA: return "CUDA error";
+        case PCOT_ERR_OOM: return "out of memory";
+        case PCOT_ERR_TIMEOUT: return "device dependency wait timed out";
+        case PCOT_ERR_BOUNDS: return "device index check failed";
+    }
+    return "unknown status";
+}
+
+pcot_status pcot_create(int dims, int radius, const double* coeffs, int ncoeffs, pcot_boundary boundary,
+                        pcot_handle* out) {
+    if (!out || !coeffs) return PCOT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (dims < 1 || dims > 3) return PCOT_ERR_UNSUPPORTED;
+    if (radius != 1) return PCOT_ERR_UNSUPPORTED;
+    if (ncoeffs != 1 + 2 * dims * radius) return PCOT_ERR_INVALID_ARG;
+    if (boundary != PCOT_DIRICHLET && boundary != PCOT_PERIODIC) return PCOT_ERR_INVALID_ARG;
+    pcot_plan* h = new pcot_plan();
+    h->dims = dims;
+    h->radius = radius;
+    h->boundary = boundary;
+    for (int i = 0; i < ncoeffs; ++i) h->coeffs[i] = coeffs[i];
+    *out = h;
+    return PCOT_OK;
+}
+
+pcot_status pcot_destroy(pcot_handle h) {
+    if (!h) return PCOT_ERR_INVALID_ARG;
+    for (auto& kv : h->cot_cache) {
+        if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+        delete kv.second;
+    }
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->d_partials) cudaFree(h->d_partials);
+    delete h;
+    return PCOT_OK;
+}
+
+pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t* sizes, const int64_t* strides, int64_t T,
+                                 pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
+                                 size_t* bytes) {
+    if (!bytes || T < 0) return PCOT_ERR_INVALID_ARG;
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, strides, dtype, nullptr, &L));
+    size_t b = twin_bytes(L);
+    if (schedule == PCOT_COT && T > 0) {
+        if (L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
+        CotPlanHost* c = nullptr;
+        PCOT_TRY(get_cot_plan(h, L, T, params, &c));
+        b += c->image_bytes;
+    }
+    *bytes = b;
+    return PCOT_OK;
+}
+
+pcot_status pcot_run(pcot_handle h, void* grid, void* workspace, const int64_t* sizes, const int64_t* strides,
+                     int64_t T, pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
+                     void* stream) {
+    return run_impl(h, grid, workspace, sizes, strides, T, dtype, schedule, params, stream);
+}
+
+pcot_status pcot_run_host(pcot_handle h, void* host_grid, void* dev_grid, void* workspace, const int64_t* sizes,
+                          const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                          const pcot_tile_params* params, void* stream) {
+    if (!host_grid || !dev_grid) return PCOT_ERR_INVALID_ARG;
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, strides, dtype, stream, &L));
+    const size_t bytes = span_bytes(L);
+    PCOT_CUDA(cudaMemcpyAsync(dev_grid, host_grid, bytes, cudaMemcpyHostToDevice, L.stream));
+    PCOT_TRY(run_impl(h, dev_grid, workspace, sizes, strides, T, dtype, schedule, params, stream));
+    PCOT_CUDA(cudaMemcpyAsync(host_grid, dev_grid, bytes, cudaMemcpyDeviceToHost, L.stream));
+    return pcot_check(h, stream);
+}
+
+pcot_status pcot_check(pcot_handle h, void* stream) {
+    if (!h) return PCOT_ERR_INVALID_ARG;
+    PCOT_TRY(ensure_device(h));
+    PCOT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    PCOT_CUDA(cudaGetLastError());
+    DevStatus st;
+    PCOT_CUDA(cudaMemcpy(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.code != 0) {
+        PCOT_CUDA(cudaMemset(h->d_status, 0, sizeof(DevStatus)));
+        return (pcot_status)st.code;
+    }
+    return PCOT_OK;
+}
+
+pcot_status pcot_plan_query(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype,
+                            const pcot_tile_params* params, int32_t* lattice, int32_t* tile_ext, int32_t* depth,
+                            int64_t* n_tiles, int64_t* tail_steps, int32_t* queue, int32_t* deps, int64_t cap) {
+    if (T < 0) return PCOT_ERR_INVALID_ARG;
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, nullptr, dtype, nullptr, &L));
+    CotPlanHost* c = nullptr;
+    PCOT_TRY(get_cot_plan(h, L, T, params, &c));
+    if (lattice)
+        for (int i = 0; i < 4; ++i) lattice[i] = c->lattice[i];
+    if (tile_ext)
+        for (int a = 0; a < 3; ++a) tile_ext[a] = (int32_t)c->tg.ext[a];
+    if (depth) *depth = c->k;
+    if (n_tiles) *n_tiles = c->ntiles;
+    if (tail_steps) {
+        int64_t s = 0;
+        for (int d : c->tail.depths) s += d;
+        *tail_steps = s;
+    }
+    if (queue || deps) {
+        if (cap < c->ntiles) return PCOT_ERR_OOM;
+        for (int64_t i = 0; i < c->ntiles; ++i) {
+            if (queue) queue[i] = c->queue[(size_t)i];
+            if (deps) deps[i] = c->counts[(size_t)c->queue[(size_t)i]];
+        }
+    }
+    return PCOT_OK;
+}
+
+pcot_status pcot_test_wait_timeout(pcot_handle h, void* workspace, int32_t timeout_ms, void* stream) {
+    if (!h || !workspace || timeout_ms < 1) return PCOT_ERR_INVALID_ARG;
+    if (((uintptr_t)workspace % 4) != 0) return PCOT_ERR_ALIGNMENT;
+    PCOT_TRY(ensure_device(h));
+    int32_t one = 1;
+    PCOT_CUDA(cudaMemcpyAsync(workspace, &one, sizeof(one), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    PCOT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    PCOT_CUDA(launch_wait_timeout_probe((int32_t*)workspace, h->d_status, (uint64_t)timeout_ms * 1000000ull,
+                                        (cudaStream_t)stream));
+    return PCOT_OK;
+}
+
+pcot_status pcot_grid_sum(pcot_handle h, const void* grid, const int64_t* sizes, const int64_t* strides,
+                          pcot_dtype dtype, double* out_device, void* stream) {
+    if (!grid || !out_device) return PCOT_ERR_INVALID_ARG;
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, strides, dtype, stream, &L));
+    if (((uintptr_t)grid % elem_size(dtype)) != 0 || ((uintptr_t)out_device % 8) != 0) return PCOT_ERR_ALIGNMENT;
+    PCOT_TRY(ensure_device(h));
+    PCOT_CUDA(launch_grid_sum(L, grid, out_device, h->d_partials, grid_sum_partials()));
+    h->launches += 2;
+    return PCOT_OK;
+}
+
+pcot_status pcot_launch_count(pcot_handle h, int64_t* launches) {
+    if (!h || !launches) return PCOT_ERR_INVALID_ARG;
+    *launches = h->launches;
+    return PCOT_OK;
+}
+
+}  // extern "C"

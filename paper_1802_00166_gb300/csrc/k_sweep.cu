@@ -1,0 +1,272 @@
+// Plain single-sweep kernels (one launch = one time step over the whole
+// grid), the Dirichlet ring copy, the FP64 interior sum and the wait probe.
+//
+// The sweep is the untiled loop nest of the paper's problem statement
+// (Sec. 4.1): every interior point of step t+1 from the 2r+1 neighbours of
+// step t along each axis, buffers alternating by t%2 (Appendix A example).
+#include "kernels.h"
+
+namespace pcot {
+
+namespace {
+
+template <class T, bool EXACT>
+__global__ void __launch_bounds__(256) sweep1d_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                      DevGeo g, Coeffs<T> c) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = g.n[0];
+    if (i >= n) return;
+    int64_t x, xm, xp;
+    if (g.periodic) {
+        x = i;
+        xm = i == 0 ? n - 1 : i - 1;
+        xp = i == n - 1 ? 0 : i + 1;
+    } else {
+        x = i + 1;
+        xm = i;
+        xp = i + 2;
+    }
+    dst[x] = upd1<T, EXACT>(c, __ldg(src + x), __ldg(src + xm), __ldg(src + xp));
+}
+
+// Thread = one column x, ROWS consecutive rows (register reuse along axis 0).
+template <class T, bool EXACT, int ROWS>
+__global__ void __launch_bounds__(256) sweep2d_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                      DevGeo g, Coeffs<T> c) {
+    const int64_t ix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t iy0 = ((int64_t)blockIdx.y * blockDim.y + threadIdx.y) * ROWS;
+    const int64_t ny = g.n[0], nx = g.n[1];
+    if (ix >= nx || iy0 >= ny) return;
+    const bool per = g.periodic != 0;
+    const int64_t P = g.s[0];
+    int64_t x, xm, xp;
+    if (per) {
+        x = ix;
+        xm = ix == 0 ? nx - 1 : ix - 1;
+        xp = ix == nx - 1 ? 0 : ix + 1;
+    } else {
+        x = ix + 1;
+        xm = ix;
+        xp = ix + 2;
+    }
+    auto row = [&](int64_t iy) -> int64_t { return per ? wrapc(iy, ny) : iy + 1; };
+    T N = __ldg(src + row(iy0 - 1) * P + x);
+    T C = __ldg(src + row(iy0) * P + x);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int64_t iy = iy0 + r;
+        if (iy >= ny) break;
+        const int64_t rs = row(iy) * P;
+        const T S = __ldg(src + row(iy + 1) * P + x);
+        const T W = __ldg(src + rs + xm);
+        const T E = __ldg(src + rs + xp);
+        dst[rs + x] = upd2<T, EXACT>(c, C, N, S, W, E);
+        N = C;
+        C = S;
+    }
+}
+
+// Thread = one (y, x) column, ZR consecutive planes along axis 0.
+template <class T, bool EXACT, int ZR>
+__global__ void __launch_bounds__(256) sweep3d_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                      DevGeo g, Coeffs<T> c) {
+    const int64_t ix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t iy = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+    const int64_t iz0 = (int64_t)blockIdx.z * ZR;
+    const int64_t nz = g.n[0], ny = g.n[1], nx = g.n[2];
+    if (ix >= nx || iy >= ny) return;
+    const bool per = g.periodic != 0;
+    const int64_t Pz = g.s[0], Py = g.s[1];
+    int64_t x, xm, xp, y, ym, yp;
+    if (per) {
+        x = ix;
+        xm = ix == 0 ? nx - 1 : ix - 1;
+        xp = ix == nx - 1 ? 0 : ix + 1;
+        y = iy;
+        ym = iy == 0 ? ny - 1 : iy - 1;
+        yp = iy == ny - 1 ? 0 : iy + 1;
+    } else {
+        x = ix + 1;
+        xm = ix;
+        xp = ix + 2;
+        y = iy + 1;
+        ym = iy;
+        yp = iy + 2;
+    }
+    auto plane = [&](int64_t iz) -> int64_t { return (per ? wrapc(iz, nz) : iz + 1) * Pz; };
+    T D = __ldg(src + plane(iz0 - 1) + y * Py + x);
+    T C = __ldg(src + plane(iz0) + y * Py + x);
+#pragma unroll
+    for (int r = 0; r < ZR; ++r) {
+        const int64_t iz = iz0 + r;
+        if (iz >= nz) break;
+        const int64_t ps = plane(iz);
+        const T U = __ldg(src + plane(iz + 1) + y * Py + x);
+        const T N = __ldg(src + ps + ym * Py + x);
+        const T S = __ldg(src + ps + yp * Py + x);
+        const T W = __ldg(src + ps + y * Py + xm);
+        const T E = __ldg(src + ps + y * Py + xp);
+        dst[ps + y * Py + x] = upd3<T, EXACT>(c, C, D, U, N, S, W, E);
+        D = C;
+        C = U;
+    }
+}
+
+template <class T>
+Coeffs<T> make_coeffs(const double* c) {
+    Coeffs<T> k;
+    for (int i = 0; i < 7; ++i) k.c[i] = (T)c[i];
+    return k;
+}
+
+template <class T, bool EXACT>
+cudaError_t sweep_t(const LaunchCtx& L, const void* src, void* dst) {
+    const DevGeo& g = L.geo;
+    const Coeffs<T> c = make_coeffs<T>(L.coeffs);
+    const T* s = (const T*)src;
+    T* d = (T*)dst;
+    if (g.dims == 1) {
+        dim3 blk(256), grd((unsigned)((g.n[0] + 255) / 256));
+        sweep1d_kernel<T, EXACT><<<grd, blk, 0, L.stream>>>(s, d, g, c);
+    } else if (g.dims == 2) {
+        constexpr int ROWS = 4;
+        dim3 blk(32, 8);
+        dim3 grd((unsigned)((g.n[1] + 31) / 32), (unsigned)((g.n[0] + 8 * ROWS - 1) / (8 * ROWS)));
+        if (grd.y > 65535) return cudaErrorInvalidConfiguration;
+        sweep2d_kernel<T, EXACT, ROWS><<<grd, blk, 0, L.stream>>>(s, d, g, c);
+    } else {
+        constexpr int ZR = 4;
+        dim3 blk(32, 8);
+        dim3 grd((unsigned)((g.n[2] + 31) / 32), (unsigned)((g.n[1] + 7) / 8), (unsigned)((g.n[0] + ZR - 1) / ZR));
+        if (grd.y > 65535 || grd.z > 65535) return cudaErrorInvalidConfiguration;
+        sweep3d_kernel<T, EXACT, ZR><<<grd, blk, 0, L.stream>>>(s, d, g, c);
+    }
+    return cudaGetLastError();
+}
+
+// Copy every cell on the outer faces (the Dirichlet ring of width 1).
+template <class T>
+__global__ void ring_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g, int64_t total) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        // Enumerate faces: for axis a, two sides, all combinations of the other axes.
+        int64_t rem = k;
+        int a = 0;
+        int64_t face = 0;
+        for (a = 0; a < g.dims; ++a) {
+            face = 1;
+            for (int b = 0; b < g.dims; ++b)
+                if (b != a) face *= g.e[b];
+            if (rem < 2 * face) break;
+            rem -= 2 * face;
+        }
+        if (a >= g.dims) continue;
+        const int side = rem >= face ? 1 : 0;
+        int64_t r = rem - side * face;
+        int64_t coord[kMaxDims] = {0, 0, 0};
+        for (int b = g.dims - 1; b >= 0; --b) {
+            if (b == a) continue;
+            coord[b] = r % g.e[b];
+            r /= g.e[b];
+        }
+        coord[a] = side ? g.e[a] - 1 : 0;
+        int64_t off = 0;
+        for (int b = 0; b < g.dims; ++b) off += coord[b] * g.s[b];
+        dst[off] = src[off];
+    }
+}
+
+// Deterministic FP64 sum of the interior: fixed blocks, fixed per-thread
+// order, fixed tree order in shared memory, then one block over the partials.
+template <class T>
+__global__ void __launch_bounds__(256) sum_partial_kernel(const T* __restrict__ grid, DevGeo g, double* partials) {
+    __shared__ double sh[256];
+    const int64_t last = g.n[g.dims - 1];
+    int64_t rows = 1;
+    for (int a = 0; a < g.dims - 1; ++a) rows *= g.n[a];
+    const int64_t off = g.periodic ? 0 : 1;
+    double acc = 0.0;
+    for (int64_t rw = blockIdx.x; rw < rows; rw += gridDim.x) {
+        int64_t rr = rw, base = 0;
+        for (int a = g.dims - 2; a >= 0; --a) {
+            base += (rr % g.n[a] + off) * g.s[a];
+            rr /= g.n[a];
+        }
+        for (int64_t x = threadIdx.x; x < last; x += blockDim.x) acc += (double)grid[base + x + off];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(256) sum_final_kernel(const double* partials, int np, double* out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+__global__ void wait_probe_kernel(int32_t* counter, DevStatus* st, uint64_t timeout_ns) {
+    if (threadIdx.x == 0) wait_zero(counter, st, timeout_ns, -1, -1);
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const LaunchCtx& L, const void* src, void* dst) {
+    switch (L.dtype) {
+        case kF32: return sweep_t<float, false>(L, src, dst);
+        case kF64: return sweep_t<double, false>(L, src, dst);
+        case kF64Exact: return sweep_t<double, true>(L, src, dst);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst) {
+    const DevGeo& g = L.geo;
+    if (g.periodic) return cudaSuccess;
+    int64_t total = 0;
+    for (int a = 0; a < g.dims; ++a) {
+        int64_t face = 1;
+        for (int b = 0; b < g.dims; ++b)
+            if (b != a) face *= g.e[b];
+        total += 2 * face;
+    }
+    const int blk = 256;
+    int64_t nb = (total + blk - 1) / blk;
+    if (nb > 4096) nb = 4096;
+    if (L.dtype == kF32)
+        ring_copy_kernel<float><<<(unsigned)nb, blk, 0, L.stream>>>((const float*)src, (float*)dst, g, total);
+    else
+        ring_copy_kernel<double><<<(unsigned)nb, blk, 0, L.stream>>>((const double*)src, (double*)dst, g, total);
+    return cudaGetLastError();
+}
+
+int grid_sum_partials() { return 1024; }
+
+cudaError_t launch_grid_sum(const LaunchCtx& L, const void* grid, double* out, double* partials, int np) {
+    if (L.dtype == kF32)
+        sum_partial_kernel<float><<<np, 256, 0, L.stream>>>((const float*)grid, L.geo, partials);
+    else
+        sum_partial_kernel<double><<<np, 256, 0, L.stream>>>((const double*)grid, L.geo, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_final_kernel<<<1, 256, 0, L.stream>>>(partials, np, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_timeout_probe(int32_t* counter, DevStatus* st, uint64_t timeout_ns, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(counter, st, timeout_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace pcot

@@ -1,0 +1,73 @@
+// Host-side launchers of the stencil kernels (implemented in the k_*.cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pcot {
+
+enum DType { kF32 = 0, kF64 = 1, kF64Exact = 2 };
+
+inline int dtype_size(int dt) { return dt == kF32 ? 4 : 8; }
+
+// Everything a launch needs about the problem.
+struct LaunchCtx {
+    DevGeo geo;
+    double coeffs[7];
+    int dtype;
+    cudaStream_t stream;
+};
+
+// Output-tile geometry of one time block (storage coordinates).
+struct TileGeo {
+    int64_t ext[kMaxDims];   // output extent of a tile per axis
+    int64_t count[kMaxDims]; // tiles per axis
+    int nwarps;              // warps per CTA (kernel specific)
+    int depth;               // time steps per tile
+    int family;              // kernel family, see below
+};
+
+enum Family { kFamGeneric = 0, kFamStream2D = 1, kFamStream3D = 2 };
+
+// Device view of a persistent-executor plan (PCOT_COT).
+struct CotDev {
+    const int32_t* queue;  // tile ids in execution order
+    int32_t* counts;       // remaining dependencies per tile id
+    int32_t* head;         // next queue position to pop
+    int64_t ntiles;
+    int32_t lattice[kMaxDims + 1];  // blocks, tiles per axis (unused axes 1)
+    DevStatus* status;
+    uint64_t timeout_ns;
+};
+
+// ---- k_sweep.cu ----
+cudaError_t launch_sweep(const LaunchCtx& L, const void* src, void* dst);
+cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst);
+cudaError_t launch_grid_sum(const LaunchCtx& L, const void* grid, double* out, double* partials,
+                            int npartials);
+int grid_sum_partials();
+
+// ---- tiled schedules ----
+// Kernel family and tile geometry for (dims, dtype, requested tile, depth).
+// Returns false when no kernel of this build supports the request.
+bool choose_tiles(const LaunchCtx& L, const int32_t* req_tile, int depth, TileGeo* out);
+// Depths a family has compiled variants for (ascending); returns the count.
+int supported_depths(int family, int dtype, int* out, int cap);
+
+// One single-level time block: all tiles of `t` read src, write dst.
+cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+// The persistent executor over a tile queue; block b reads buf[b%2], writes buf[(b+1)%2].
+cudaError_t launch_cot(const LaunchCtx& L, const TileGeo& t, void* buf0, void* buf1,
+                       const CotDev& q, int num_ctas);
+// Resident CTAs per SM of the persistent executor for this geometry.
+int cot_ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
+// Dynamic shared memory of one CTA for this geometry.
+size_t tile_smem_bytes(const LaunchCtx& L, const TileGeo& t);
+
+// ---- k_misc ----
+cudaError_t launch_wait_timeout_probe(int32_t* counter, DevStatus* st, uint64_t timeout_ns,
+                                      cudaStream_t s);
+
+}  // namespace pcot

@@ -1,0 +1,91 @@
+// Internal interface between the kernel families and the dispatcher.
+#pragma once
+
+#include "kernels.h"
+
+namespace pcot {
+
+template <int U>
+struct IC {
+    static constexpr int value = U;
+};
+
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int E = 4;
+};
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int E = 2;
+};
+
+template <class T>
+inline Coeffs<T> coeffs_as(const double* c) {
+    Coeffs<T> k;
+    for (int i = 0; i < 7; ++i) k.c[i] = (T)c[i];
+    return k;
+}
+
+// Release the dependency counters of the successors of lattice tile
+// (b, i0, i1, i2): every (b+1, j) with |j_a - i_a| <= 1 inside the lattice.
+__device__ __forceinline__ void release_successors(const CotDev& q, int dims, int b, int i0, int i1, int i2) {
+    if (b + 1 >= q.lattice[0]) return;
+    const int L0 = q.lattice[1], L1 = q.lattice[2], L2 = q.lattice[3];
+    for (int d0 = -1; d0 <= 1; ++d0) {
+        const int j0 = i0 + d0;
+        if (j0 < 0 || j0 >= L0) continue;
+        for (int d1 = (dims > 1 ? -1 : 0); d1 <= (dims > 1 ? 1 : 0); ++d1) {
+            const int j1 = i1 + d1;
+            if (j1 < 0 || j1 >= L1) continue;
+            for (int d2 = (dims > 2 ? -1 : 0); d2 <= (dims > 2 ? 1 : 0); ++d2) {
+                const int j2 = i2 + d2;
+                if (j2 < 0 || j2 >= L2) continue;
+                const int id = (((b + 1) * L0 + j0) * L1 + j1) * L2 + j2;
+                red_release_add_gpu(q.counts + id, -1);
+            }
+        }
+    }
+}
+
+// Pop the next queue entry and wait for its dependencies (thread 0 only).
+// Returns the tile id, or -1 when the queue is exhausted or a wait gave up.
+__device__ __forceinline__ int pop_and_wait(const CotDev& q) {
+    const int pos = atomicAdd(q.head, 1);
+    if (pos >= q.ntiles) return -1;
+    const int tile = q.queue[pos];
+    if (!wait_zero(q.counts + tile, q.status, q.timeout_ns, tile, pos)) return -1;
+    __threadfence();
+    return tile;
+}
+
+// Family entry points (one per kernel family).
+namespace stream2d {
+bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t);
+int depths(int dtype, int* out, int cap);
+cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas);
+int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
+}  // namespace stream2d
+
+namespace stream3d {
+bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t);
+int depths(int dtype, int* out, int cap);
+cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas);
+int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
+size_t smem(const LaunchCtx& L, const TileGeo& t);
+}  // namespace stream3d
+
+namespace generic {
+bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t);
+cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas);
+int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
+size_t smem(const LaunchCtx& L, const TileGeo& t);
+}  // namespace generic
+
+}  // namespace pcot

@@ -1,0 +1,235 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+FP64 exact mode must be bitwise equal to the oracle for every schedule (the
+schedules only reorder legal computations, Sec. 3.1 / Sec. 4.2).  FP32 must
+stay within max-relative error 1e-5 of the oracle run on the widened FP32
+inputs (normwise, max|u - ref| / max|ref|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+
+torch = pytest.importorskip("torch")
+pcot = pytest.importorskip("paper_1802_00166_gb300")
+from tests.gpu_util import COEFFS, HEAT2D, JAC1D, JAC3D, padded_strides, run_gpu  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+SCHEDS = [pcot.PCOT_SWEEP, pcot.PCOT_SLT, pcot.PCOT_COT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00166_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _handle(dims, periodic=False, coeffs=None):
+    return pcot.pcot_create(dims, 1, COEFFS[dims] if coeffs is None else coeffs,
+                            pcot.PCOT_PERIODIC if periodic else pcot.PCOT_DIRICHLET)
+
+
+# ---------------------------------------------------------------- 1-D ----
+
+@pytest.mark.parametrize("n", [1, 2, 5, 37, 100, 1000])
+@pytest.mark.parametrize("T", [0, 1, 2, 3, 7, 16, 45])
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_jacobi1d_exact(n, T, sched):
+    h = _handle(1)
+    g = si.uniform_grid((n,), 1, ring="random")
+    ref = oracle.sweep(g, (n,), JAC1D, T)
+    for params in (None, pcot.tile_params(tile=(7,), time_depth=3, cot_threshold=(2, 2))):
+        got = run_gpu(h, g, (n,), T, pcot.PCOT_F64_EXACT, sched, params)
+        assert np.array_equal(got, ref), (n, T, sched)
+    pcot.pcot_destroy(h)
+
+
+def test_jacobi1d_periodic_exact():
+    h = _handle(1, periodic=True)
+    g = si.uniform_grid((301,), 3, periodic=True)
+    for sched in (pcot.PCOT_SWEEP, pcot.PCOT_SLT):
+        got = run_gpu(h, g, (301,), 57, pcot.PCOT_F64_EXACT, sched)
+        assert np.array_equal(got, oracle.sweep(g, (301,), JAC1D, 57, periodic=True))
+    pcot.pcot_destroy(h)
+
+
+# ---------------------------------------------------------------- 2-D ----
+
+SIZES2 = [(1, 1), (3, 5), (33, 130), (130, 333), (257, 1000)]
+
+
+@pytest.mark.parametrize("sizes", SIZES2)
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_heat2d_exact(sizes, sched):
+    h = _handle(2)
+    g = si.uniform_grid(sizes, 2)
+    for T in (1, 4, 11):
+        ref = oracle.sweep(g, sizes, HEAT2D, T)
+        got = run_gpu(h, g, sizes, T, pcot.PCOT_F64_EXACT, sched)
+        assert np.array_equal(got, ref), (sizes, T, sched)
+    pcot.pcot_destroy(h)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("sched", [pcot.PCOT_SLT, pcot.PCOT_COT])
+def test_heat2d_exact_depths_and_tiles(k, sched):
+    """Every compiled depth plus one that falls to the generic kernel (5),
+    ragged tiles in both axes, several recursion thresholds."""
+    h = _handle(2, coeffs=si.random_coefficients(2, 1, 40 + k))
+    c = si.random_coefficients(2, 1, 40 + k)
+    sizes = (97, 301)
+    g = si.uniform_grid(sizes, 5, ring="random")
+    T = 3 * k + 5
+    ref = oracle.sweep(g, sizes, c, T)
+    for tile, th in (((8, 0), (1, 1, 1)), ((13, 130), (2, 4, 1)), ((32, 500), (4, 2, 2))):
+        p = pcot.tile_params(tile=tile, time_depth=k, cot_threshold=th)
+        got = run_gpu(h, g, sizes, T, pcot.PCOT_F64_EXACT, sched, p)
+        assert np.array_equal(got, ref), (k, tile, th)
+    pcot.pcot_destroy(h)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("k", [1, 2, 4, 6, 8])
+def test_heat2d_f32_within_tolerance(sched, k):
+    h = _handle(2)
+    sizes = (190, 517)
+    g32 = si.uniform_grid(sizes, 2, dtype=np.float32)
+    T = 40
+    ref = oracle.sweep(g32, sizes, HEAT2D, T)
+    p = pcot.tile_params(tile=(24, 0), time_depth=k, cot_threshold=(2, 2, 2))
+    got = run_gpu(h, g32, sizes, T, pcot.PCOT_F32, sched, p)
+    assert oracle.max_rel_error(oracle.interior(got, sizes), oracle.interior(ref, sizes)) <= F32_TOL
+    assert np.array_equal(got[0], g32[0]) and np.array_equal(got[:, -1], g32[:, -1])  # ring untouched
+    pcot.pcot_destroy(h)
+
+
+def test_heat2d_periodic():
+    h = _handle(2, periodic=True)
+    sizes = (64, 256)
+    g = si.uniform_grid(sizes, 9, periodic=True)
+    ref = oracle.sweep(g, sizes, HEAT2D, 13, periodic=True)
+    for sched in (pcot.PCOT_SWEEP, pcot.PCOT_SLT):
+        for k in (1, 3, 4):
+            got = run_gpu(h, g, sizes, 13, pcot.PCOT_F64_EXACT, sched, pcot.tile_params(tile=(16, 0), time_depth=k))
+            assert np.array_equal(got, ref), (sched, k)
+    pcot.pcot_destroy(h)
+
+
+def test_heat2d_strided_layout_equals_contiguous():
+    h = _handle(2)
+    sizes = (70, 250)
+    g = si.uniform_grid(sizes, 4)
+    ref = oracle.sweep(g, sizes, HEAT2D, 9)
+    shape = g.shape
+    for sched in SCHEDS:
+        st = padded_strides(shape, 8, 64)
+        got = run_gpu(h, g, sizes, 9, pcot.PCOT_F64_EXACT, sched, strides=st)
+        assert np.array_equal(got, ref)
+    pcot.pcot_destroy(h)
+
+
+def test_checkpoint_resume_bitwise():
+    """The state after t steps is the grid: run(T1); run(T2) == run(T1 + T2)."""
+    h = _handle(2)
+    sizes = (50, 200)
+    g = si.uniform_grid(sizes, 6)
+    a = run_gpu(h, g, sizes, 7, pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
+    a = run_gpu(h, a, sizes, 10, pcot.PCOT_F64_EXACT, pcot.PCOT_SLT)
+    b = run_gpu(h, g, sizes, 17, pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
+    assert np.array_equal(a, b)
+    pcot.pcot_destroy(h)
+
+
+# ---------------------------------------------------------------- 3-D ----
+
+@pytest.mark.parametrize("sizes", [(3, 4, 5), (20, 33, 70), (40, 21, 130)])
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_jacobi3d_exact_dirichlet(sizes, sched):
+    h = _handle(3)
+    g = si.uniform_grid(sizes, 8, ring="random")
+    for T, k in ((1, 1), (5, 2), (6, 3)):
+        ref = oracle.sweep(g, sizes, JAC3D, T)
+        got = run_gpu(h, g, sizes, T, pcot.PCOT_F64_EXACT, sched, pcot.tile_params(tile=(8, 0, 0), time_depth=k))
+        assert np.array_equal(got, ref), (sizes, T, k, sched)
+    pcot.pcot_destroy(h)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_jacobi3d_periodic_f32_and_exact(k):
+    h = _handle(3, periodic=True)
+    sizes = (24, 40, 96)
+    g, _ = si.fourier_grid(sizes, 3)
+    T = 2 * k + 3
+    ref = oracle.sweep(g, sizes, JAC3D, T, periodic=True)
+    p = pcot.tile_params(tile=(8, 0, 0), time_depth=k)
+    got32 = run_gpu(h, g.astype(np.float32), sizes, T, pcot.PCOT_F32, pcot.PCOT_SLT, p)
+    ref32 = oracle.sweep(g.astype(np.float32), sizes, JAC3D, T, periodic=True)
+    assert oracle.max_rel_error(got32, ref32) <= F32_TOL
+    if k <= 2:
+        got = run_gpu(h, g, sizes, T, pcot.PCOT_F64_EXACT, pcot.PCOT_SLT, p)
+        assert np.array_equal(got, ref)
+    got = run_gpu(h, g, sizes, T, pcot.PCOT_F64_EXACT, pcot.PCOT_SWEEP)
+    assert np.array_equal(got, ref)
+    pcot.pcot_destroy(h)
+
+
+# ------------------------------------------------------- status / sums ----
+
+def test_timeout_is_reported_not_hung():
+    h = _handle(2)
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    pcot.pcot_test_wait_timeout(h, ws.data_ptr(), 200)
+    assert pcot.pcot_check(h) == pcot.PCOT_ERR_TIMEOUT
+    assert pcot.pcot_check(h) == pcot.PCOT_OK   # cleared, context still usable
+    g = si.uniform_grid((10, 10), 1)
+    assert np.array_equal(run_gpu(h, g, (10, 10), 3, pcot.PCOT_F64_EXACT, pcot.PCOT_COT),
+                          oracle.sweep(g, (10, 10), HEAT2D, 3))
+    pcot.pcot_destroy(h)
+
+
+def test_misaligned_workspace_rejected():
+    h = _handle(2)
+    g = torch.zeros((12, 12), dtype=torch.float64, device="cuda")
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pcot.PcotError) as e:
+        pcot.pcot_run(h, g.data_ptr(), ws.data_ptr() + 8, (10, 10), None, 2, pcot.PCOT_F64_EXACT, pcot.PCOT_SLT)
+    assert e.value.status == pcot.PCOT_ERR_ALIGNMENT
+    pcot.pcot_destroy(h)
+
+
+@pytest.mark.parametrize("dims,sizes,periodic", [(1, (1000,), False), (2, (300, 257), False),
+                                                 (3, (30, 40, 50), True)])
+def test_grid_sum(dims, sizes, periodic):
+    h = _handle(dims, periodic)
+    g = si.uniform_grid(sizes, 11, periodic=periodic, ring="random")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dev = torch.from_numpy(g).cuda()
+    pcot.pcot_grid_sum(h, dev.data_ptr(), sizes, None, pcot.PCOT_F64, out.data_ptr())
+    s = float(out.item())
+    exact = oracle.grid_sum(g, sizes, periodic=periodic)
+    assert abs(s - exact) <= 1e-12 * abs(exact)
+    dev32 = torch.from_numpy(g.astype(np.float32)).cuda()
+    pcot.pcot_grid_sum(h, dev32.data_ptr(), sizes, None, pcot.PCOT_F32, out.data_ptr())
+    exact32 = oracle.grid_sum(g.astype(np.float32), sizes, periodic=periodic)
+    assert abs(float(out.item()) - exact32) <= 1e-12 * abs(exact32)
+    pcot.pcot_destroy(h)
+
+
+def test_run_host_end_to_end():
+    h = _handle(2)
+    sizes = (64, 300)
+    g = si.uniform_grid(sizes, 12)
+    host = torch.from_numpy(g.copy()).pin_memory()
+    dev = torch.empty_like(host, device="cuda")
+    nb = pcot.pcot_workspace_bytes(h, sizes, None, 10, pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    pcot.pcot_run_host(h, host.data_ptr(), dev.data_ptr(), ws.data_ptr(), sizes, None, 10,
+                       pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
+    assert np.array_equal(host.numpy(), oracle.sweep(g, sizes, HEAT2D, 10))
+    pcot.pcot_destroy(h)
