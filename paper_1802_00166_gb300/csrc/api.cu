@@ -238,7 +238,7 @@ pcot_status run_blocks(pcot_handle h, const LaunchCtx& L, const pcot_tile_params
     for (int d : bp.depths) {
         TileGeo tg;
         if (!choose_tiles(L, p ? p->tile : nullptr, d, &tg)) return PCOT_ERR_UNSUPPORTED;
-        PCOT_CUDA(launch_slt_block(L, tg, cur, other));
+        PCOT_CUDA(launch_slt_block(L, tg, cur, other, h->d_status));
         ++h->launches;
         std::swap(cur, other);
     }

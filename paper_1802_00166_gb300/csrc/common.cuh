@@ -87,6 +87,14 @@ __device__ __forceinline__ int64_t wrapc(int64_t x, int64_t n) {
     return r < 0 ? r + n : r;
 }
 
+// Wrap without 64-bit division for coordinates within one period of [0, n).
+__device__ __forceinline__ int64_t wrap_fast(int64_t x, int64_t n) {
+    if (x >= 0 && x < n) return x;
+    if (x < 0 && x >= -n) return x + n;
+    if (x >= n && x < 2 * n) return x - n;
+    return wrapc(x, n);
+}
+
 // Interior test of one storage coordinate.
 __device__ __forceinline__ bool interior_c(int64_t x, int64_t n, bool periodic) {
     return periodic ? true : (x >= 1 && x <= n);

@@ -57,7 +57,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     int64_t ysrc;
     bool yin, yint;
     if (per) {
-        ysrc = wrapc(y, ny);
+        ysrc = wrap_fast(y, ny);
         yin = true;
         yint = true;
     } else {
@@ -74,7 +74,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     for (int j = 0; j < E; ++j) {
         const int64_t x = xl + j;
         if (per) {
-            col[j] = wrapc(x, nx);
+            col[j] = wrap_fast(x, nx);
             inb[j] = true;
             xint[j] = true;
         } else {
@@ -96,7 +96,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         int64_t zs;
         bool zin;
         if (per) {
-            zs = wrapc(zi, nz);
+            zs = wrap_fast(zi, nz);
             zin = true;
         } else {
             zs = zi;
@@ -132,16 +132,18 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             for (int j = 0; j < E; ++j) R[s][u][j] = T(0);
 
     const int64_t zbeg = z0 - K, zend = z0 + Hz + K;
-    T pf[E];
-    load_plane(zbeg, pf);
+    T pf[3][E];  // three planes in flight per lane
+    load_plane(zbeg, pf[0]);
+    if (zbeg + 1 < zend) load_plane(zbeg + 1, pf[1]);
+    if (zbeg + 2 < zend) load_plane(zbeg + 2, pf[2]);
     int buf = 0;
 
     auto step = [&](auto Uc, int64_t zi) {
         constexpr int U = decltype(Uc)::value;
         constexpr int SA = U % 3, SB = (U + 1) % 3, SN = (U + 2) % 3;
-        R[0][SN][0] = pf[0];
-        R[0][SN][1] = pf[1];
-        if (zi + 1 < zend) load_plane(zi + 1, pf);
+        R[0][SN][0] = pf[U][0];
+        R[0][SN][1] = pf[U][1];
+        if (zi + 3 < zend) load_plane(zi + 3, pf[U]);
         T* smb = sm + buf * buf_stride;
 #pragma unroll
         for (int s = 0; s < K; ++s) {

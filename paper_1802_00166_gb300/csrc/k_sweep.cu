@@ -4,7 +4,7 @@
 // The sweep is the untiled loop nest of the paper's problem statement
 // (Sec. 4.1): every interior point of step t+1 from the 2r+1 neighbours of
 // step t along each axis, buffers alternating by t%2 (Appendix A example).
-#include "kernels.h"
+#include "tiled.cuh"
 
 namespace pcot {
 
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) sweep2d_kernel(const T* __restrict__ src,
         xm = ix;
         xp = ix + 2;
     }
-    auto row = [&](int64_t iy) -> int64_t { return per ? wrapc(iy, ny) : iy + 1; };
+    auto row = [&](int64_t iy) -> int64_t { return per ? wrap_fast(iy, ny) : iy + 1; };
     T N = __ldg(src + row(iy0 - 1) * P + x);
     T C = __ldg(src + row(iy0) * P + x);
 #pragma unroll
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const T* __restrict__ src,
         ym = iy;
         yp = iy + 2;
     }
-    auto plane = [&](int64_t iz) -> int64_t { return (per ? wrapc(iz, nz) : iz + 1) * Pz; };
+    auto plane = [&](int64_t iz) -> int64_t { return (per ? wrap_fast(iz, nz) : iz + 1) * Pz; };
     T D = __ldg(src + plane(iz0 - 1) + y * Py + x);
     T C = __ldg(src + plane(iz0) + y * Py + x);
 #pragma unroll
@@ -112,6 +112,172 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const T* __restrict__ src,
     }
 }
 
+
+// Vectorised sweeps: a warp covers 32*E contiguous storage columns (one
+// 16-byte vector per lane) of R rows (2-D) or R planes of one row (3-D); every
+// row it needs is loaded up front so R+2 (2-D) or 3R+2 (3-D) vector loads per
+// lane are in flight; x-neighbours come from warp shuffles plus one scalar
+// load at each end of the span.  Used when rows are 16-byte aligned and, for
+// periodic grids, the contiguous extent is a multiple of the warp span.
+template <class T, bool EXACT, int R>
+__global__ void __launch_bounds__(256) sweep2d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
+                                                          Coeffs<T> c) {
+    constexpr int E = Vec<T>::E;
+    using V = typename Vec<T>::V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool per = g.periodic != 0;
+    const int64_t ny = g.n[0], nx = g.n[1], ex = g.e[1], P = g.s[0];
+    const int64_t off = per ? 0 : 1;
+    const int64_t x0 = (int64_t)blockIdx.x * (32 * E);
+    const int64_t xl = x0 + lane * E;
+    const int64_t iy0 = ((int64_t)blockIdx.y * (blockDim.x >> 5) + warp) * R;  // first interior row
+    if (iy0 >= ny) return;
+    auto srow = [&](int64_t iy) -> int64_t { return per ? wrap_fast(iy, ny) : iy + 1; };
+    const bool full = xl + E <= ex;
+    T v[R + 2][E];
+#pragma unroll
+    for (int i = 0; i < R + 2; ++i) {
+        const int64_t iy = iy0 - 1 + i;
+        const bool ok = iy <= ny;  // rows past the far ring are never needed
+        const T* rp = src + srow(iy) * P;
+        if (ok && full) {
+            const V q = __ldg(reinterpret_cast<const V*>(rp + xl));
+            const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[i][j] = qq[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[i][j] = (ok && xl + j < ex) ? __ldg(rp + xl + j) : T(0);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int64_t iy = iy0 + i;
+        if (iy >= ny) break;
+        const T* rp = src + srow(iy) * P;
+        T wl = __shfl_up_sync(0xffffffffu, v[i + 1][E - 1], 1);
+        T er = __shfl_down_sync(0xffffffffu, v[i + 1][0], 1);
+        if (lane == 0) {
+            const int64_t xm = x0 - 1;
+            wl = per ? __ldg(rp + wrap_fast(xm, nx)) : (xm >= 0 ? __ldg(rp + xm) : T(0));
+        }
+        if (lane == 31) {
+            const int64_t xp = x0 + 32 * E;
+            er = per ? __ldg(rp + wrap_fast(xp, nx)) : (xp < ex ? __ldg(rp + xp) : T(0));
+        }
+        T out[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const T W = j > 0 ? v[i + 1][j - 1] : wl;
+            const T Ea = j < E - 1 ? v[i + 1][j + 1] : er;
+            out[j] = upd2<T, EXACT>(c, v[i + 1][j], v[i][j], v[i + 2][j], W, Ea);
+        }
+        T* wp = dst + (iy + off) * P;
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < E; ++j) all = all && (xl + j >= off) && (xl + j < off + nx);
+        if (all) {
+            V q;
+            T* qq = reinterpret_cast<T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) qq[j] = out[j];
+            *reinterpret_cast<V*>(wp + xl) = q;
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if (xl + j >= off && xl + j < off + nx) wp[xl + j] = out[j];
+        }
+    }
+}
+
+template <class T, bool EXACT, int R>
+__global__ void __launch_bounds__(256) sweep3d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
+                                                          Coeffs<T> c) {
+    constexpr int E = Vec<T>::E;
+    using V = typename Vec<T>::V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool per = g.periodic != 0;
+    const int64_t nz = g.n[0], ny = g.n[1], nx = g.n[2], ex = g.e[2], Pz = g.s[0], Py = g.s[1];
+    const int64_t off = per ? 0 : 1;
+    const int64_t x0 = (int64_t)blockIdx.x * (32 * E);
+    const int64_t xl = x0 + lane * E;
+    const int64_t iy = (int64_t)blockIdx.y * (blockDim.x >> 5) + warp;
+    const int64_t iz0 = (int64_t)blockIdx.z * R;
+    if (iy >= ny) return;
+    auto sz = [&](int64_t iz) -> int64_t { return per ? wrap_fast(iz, nz) : iz + 1; };
+    auto sy = [&](int64_t jy) -> int64_t { return per ? wrap_fast(jy, ny) : jy + 1; };
+    const bool full = xl + E <= ex;
+    auto ld = [&](int64_t base, T (&v)[E], bool ok) {
+        if (ok && full) {
+            const V q = __ldg(reinterpret_cast<const V*>(src + base + xl));
+            const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[j] = qq[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) v[j] = (ok && xl + j < ex) ? __ldg(src + base + xl + j) : T(0);
+        }
+    };
+    const int64_t yc = sy(iy) * Py, yn = sy(iy - 1) * Py, ys = sy(iy + 1) * Py;
+    T C[R + 2][E], N[R][E], S[R][E];
+#pragma unroll
+    for (int i = 0; i < R + 2; ++i) ld(sz(iz0 - 1 + i) * Pz + yc, C[i], iz0 - 1 + i <= nz);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const bool ok = iz0 + i < nz;
+        ld(sz(iz0 + i) * Pz + yn, N[i], ok);
+        ld(sz(iz0 + i) * Pz + ys, S[i], ok);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int64_t iz = iz0 + i;
+        if (iz >= nz) break;
+        const T* rp = src + sz(iz) * Pz + yc;
+        T wl = __shfl_up_sync(0xffffffffu, C[i + 1][E - 1], 1);
+        T er = __shfl_down_sync(0xffffffffu, C[i + 1][0], 1);
+        if (lane == 0) {
+            const int64_t xm = x0 - 1;
+            wl = per ? __ldg(rp + wrap_fast(xm, nx)) : (xm >= 0 ? __ldg(rp + xm) : T(0));
+        }
+        if (lane == 31) {
+            const int64_t xp = x0 + 32 * E;
+            er = per ? __ldg(rp + wrap_fast(xp, nx)) : (xp < ex ? __ldg(rp + xp) : T(0));
+        }
+        T out[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const T W = j > 0 ? C[i + 1][j - 1] : wl;
+            const T Ea = j < E - 1 ? C[i + 1][j + 1] : er;
+            out[j] = upd3<T, EXACT>(c, C[i + 1][j], C[i][j], C[i + 2][j], N[i][j], S[i][j], W, Ea);
+        }
+        T* wp = dst + sz(iz) * Pz + yc;
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < E; ++j) all = all && (xl + j >= off) && (xl + j < off + nx);
+        if (all) {
+            V q;
+            T* qq = reinterpret_cast<T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) qq[j] = out[j];
+            *reinterpret_cast<V*>(wp + xl) = q;
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                if (xl + j >= off && xl + j < off + nx) wp[xl + j] = out[j];
+        }
+    }
+}
+
+template <class T>
+bool sweep_vec_ok(const DevGeo& g, const void* a, const void* b) {
+    constexpr int E = Vec<T>::E;
+    if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;
+    for (int d = 0; d < g.dims - 1; ++d)
+        if ((g.s[d] * (int64_t)sizeof(T)) & 15) return false;
+    if (g.periodic && (g.n[g.dims - 1] % (32 * E)) != 0) return false;
+    return g.dims >= 2;
+}
+
 template <class T>
 Coeffs<T> make_coeffs(const double* c) {
     Coeffs<T> k;
@@ -128,6 +294,19 @@ cudaError_t sweep_t(const LaunchCtx& L, const void* src, void* dst) {
     if (g.dims == 1) {
         dim3 blk(256), grd((unsigned)((g.n[0] + 255) / 256));
         sweep1d_kernel<T, EXACT><<<grd, blk, 0, L.stream>>>(s, d, g, c);
+    } else if (g.dims == 2 && sweep_vec_ok<T>(g, src, dst)) {
+        constexpr int R = 8;
+        constexpr int E = Vec<T>::E;
+        dim3 grd((unsigned)((g.e[1] + 32 * E - 1) / (32 * E)), (unsigned)((g.n[0] + 8 * R - 1) / (8 * R)));
+        if (grd.y > 65535) return cudaErrorInvalidConfiguration;
+        sweep2d_vec_kernel<T, EXACT, R><<<grd, 256, 0, L.stream>>>(s, d, g, c);
+    } else if (g.dims == 3 && sweep_vec_ok<T>(g, src, dst)) {
+        constexpr int R = 4;
+        constexpr int E = Vec<T>::E;
+        dim3 grd((unsigned)((g.e[2] + 32 * E - 1) / (32 * E)), (unsigned)((g.n[1] + 7) / 8),
+                 (unsigned)((g.n[0] + R - 1) / R));
+        if (grd.y > 65535 || grd.z > 65535) return cudaErrorInvalidConfiguration;
+        sweep3d_vec_kernel<T, EXACT, R><<<grd, 256, 0, L.stream>>>(s, d, g, c);
     } else if (g.dims == 2) {
         constexpr int ROWS = 4;
         dim3 blk(32, 8);

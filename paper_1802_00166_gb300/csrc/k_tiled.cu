@@ -1,5 +1,8 @@
 // Dispatch from (dims, dtype, depth) to a kernel family.
+#include <cudaTypedefs.h>
+
 #include "tiled.cuh"
+#include "tma.cuh"
 
 namespace pcot {
 
@@ -15,9 +18,9 @@ int supported_depths(int family, int dtype, int* out, int cap) {
     return 0;  // any depth
 }
 
-cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst) {
+cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst, DevStatus* st) {
     switch (t.family) {
-        case kFamStream2D: return stream2d::slt(L, t, src, dst);
+        case kFamStream2D: return stream2d::slt(L, t, src, dst, st);
         case kFamStream3D: return stream3d::slt(L, t, src, dst);
         default: return generic::slt(L, t, src, dst);
     }
@@ -45,6 +48,31 @@ size_t tile_smem_bytes(const LaunchCtx& L, const TileGeo& t) {
         case kFamStream3D: return stream3d::smem(L, t);
         default: return generic::smem(L, t);
     }
+}
+
+bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t width, uint64_t height,
+                    uint64_t pitch_bytes, uint32_t box_w, uint32_t box_h) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    if (!fn || !base || ((uintptr_t)base & 15) || (pitch_bytes & 15) || box_w > 256 || box_h > 256) return false;
+    const cuuint64_t dims[2] = {width, height};
+    const cuuint64_t strides[1] = {pitch_bytes};
+    const cuuint32_t box[2] = {box_w, box_h};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r =
+        fn(map, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+           const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 }  // namespace pcot

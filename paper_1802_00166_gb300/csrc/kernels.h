@@ -56,8 +56,10 @@ bool choose_tiles(const LaunchCtx& L, const int32_t* req_tile, int depth, TileGe
 // Depths a family has compiled variants for (ascending); returns the count.
 int supported_depths(int family, int dtype, int* out, int cap);
 
-// One single-level time block: all tiles of `t` read src, write dst.
-cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+// One single-level time block: all tiles of `t` read src, write dst.  `st`
+// (may be NULL) is the status block bounded waits report to; without it the
+// kernels use plain loads instead of the TMA ring.
+cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst, DevStatus* st);
 // The persistent executor over a tile queue; block b reads buf[b%2], writes buf[(b+1)%2].
 cudaError_t launch_cot(const LaunchCtx& L, const TileGeo& t, void* buf0, void* buf1,
                        const CotDev& q, int num_ctas);

@@ -66,7 +66,7 @@ __device__ __forceinline__ int pop_and_wait(const CotDev& q) {
 namespace stream2d {
 bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t);
 int depths(int dtype, int* out, int cap);
-cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst);
+cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst, DevStatus* st);
 cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas);
 int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
 }  // namespace stream2d
