@@ -33,7 +33,8 @@ HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
 METRIC = "GUpdates/s & DRAM bytes/update vs plain sweep; % HBM roofline at stated error"
 UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
-BEST = {"schedule": "slt", "tile": (128, 220), "time_depth": 8, "cot_threshold": (2, 64, 64)}
+BEST = {"schedule": "slt", "tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
+BEST_COT = {"schedule": "cot", "tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 
@@ -215,7 +216,7 @@ def run_gpu(args):
     wsbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
 
     def step():
-        pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, pcot.PCOT_F32, sched,
+        pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), nb, sizes, strides, T_STEPS, pcot.PCOT_F32, sched,
                       params, stream)
 
     for _ in range(args.warmup):
@@ -257,7 +258,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        pcot.pcot_run_host(h, host.data_ptr(), base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS,
+        pcot.pcot_run_host(h, host.data_ptr(), base.data_ptr(), wsbuf.data_ptr(), nb, sizes, strides, T_STEPS,
                            pcot.PCOT_F32, sched, params, stream)
     e2e_dt = time.perf_counter() - t0
     span = (shape[0] - 1) * pitch + shape[1]
@@ -304,7 +305,7 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
     if args.schedules and rank == 0:
-        line["schedules"] = compare_schedules(pcot, h, base, wsbuf, sizes, strides, stream)
+        line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
     pcot.pcot_destroy(h)
     if rank == 0:
         print(json.dumps(line))
@@ -313,27 +314,36 @@ def run_gpu(args):
     return 0
 
 
-def compare_schedules(pcot, h, base, wsbuf, sizes, strides, stream):
-    """Context numbers: sweep / SLT / COT in FP32 and the FP64 modes."""
+def compare_schedules(pcot, h, base, sizes, strides, stream):
+    """Context numbers: the plain sweep, SLT and COT in FP32 (own workspaces)."""
     import torch
     out = {}
-    cases = [("sweep_f32", pcot.PCOT_SWEEP, pcot.PCOT_F32, None),
-             ("slt_f32", pcot.PCOT_SLT, pcot.PCOT_F32, BEST),
-             ("cot_f32", pcot.PCOT_COT, pcot.PCOT_F32, BEST)]
-    for name, sched, dt, p in cases:
-        prm = None if p is None else pcot.tile_params(tile=p["tile"], time_depth=p["time_depth"],
-                                                      cot_threshold=p["cot_threshold"])
-        pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, dt, sched, prm, stream)
+    prm = pcot.tile_params(tile=BEST["tile"], time_depth=BEST["time_depth"], cot_threshold=BEST["cot_threshold"])
+    cot_prm = pcot.tile_params(tile=BEST_COT["tile"], time_depth=BEST_COT["time_depth"],
+                               cot_threshold=BEST_COT["cot_threshold"])
+    cases = [("sweep_f32", pcot.PCOT_SWEEP, None), ("slt_f32", pcot.PCOT_SLT, prm), ("cot_f32", pcot.PCOT_COT, cot_prm)]
+    for name, sched, p in cases:
+        nb = pcot.pcot_workspace_bytes(h, sizes, strides, T_STEPS, pcot.PCOT_F32, sched, p)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        run = lambda: pcot.pcot_run(h, base.data_ptr(), ws.data_ptr(), nb, sizes, strides, T_STEPS,
+                                    pcot.PCOT_F32, sched, p, stream)
+        run()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(3):
-            pcot.pcot_run(h, base.data_ptr(), wsbuf.data_ptr(), sizes, strides, T_STEPS, dt, sched, prm, stream)
+            run()
         e1.record(stream)
         torch.cuda.synchronize()
+        st = pcot.pcot_check(h, stream)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, name)
         ms = e0.elapsed_time(e1) / 3
         out[name] = {"ms": ms, "GUpdates/s": N_SIDE * N_SIDE * T_STEPS / ms / 1e6}
+        if p is not None:
+            out[name]["params"] = {"tile": list(p.tile)[:2], "time_depth": p.time_depth,
+                                   "cot_threshold": list(p.cot_threshold)[:3]}
     return out
 
 

@@ -133,13 +133,15 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t *sizes, const int6
  *  workspace  device scratch of at least pcot_workspace_bytes bytes, 256-byte
  *             aligned; its contents on entry are ignored and on exit are
  *             undefined.  The Dirichlet ring is copied into it by the call.
+ *  workspace_bytes  size of `workspace`; a smaller size than the schedule
+ *             needs returns PCOT_ERR_OOM before anything is launched.
  *  T          number of time steps, T >= 0; T = 0 returns PCOT_OK at once.
  *  schedule   PCOT_AUTO picks with the built-in defaults.
  *  params     NULL = defaults.
  * Asynchronous on `stream`; call pcot_check to surface device errors.
  */
-pcot_status pcot_run(pcot_handle h, void *grid, void *workspace, const int64_t *sizes,
-                     const int64_t *strides, int64_t T, pcot_dtype dtype,
+pcot_status pcot_run(pcot_handle h, void *grid, void *workspace, size_t workspace_bytes,
+                     const int64_t *sizes, const int64_t *strides, int64_t T, pcot_dtype dtype,
                      pcot_schedule schedule, const pcot_tile_params *params, void *stream);
 
 /*
@@ -149,7 +151,7 @@ pcot_status pcot_run(pcot_handle h, void *grid, void *workspace, const int64_t *
  * stream before returning (so it also reports device errors like pcot_check).
  */
 pcot_status pcot_run_host(pcot_handle h, void *host_grid, void *dev_grid, void *workspace,
-                          const int64_t *sizes, const int64_t *strides, int64_t T,
+                          size_t workspace_bytes, const int64_t *sizes, const int64_t *strides, int64_t T,
                           pcot_dtype dtype, pcot_schedule schedule,
                           const pcot_tile_params *params, void *stream);
 

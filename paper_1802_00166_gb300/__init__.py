@@ -83,10 +83,10 @@ def _load():
         "pcot_destroy": (S, [_VP]),
         "pcot_workspace_bytes": (S, [_VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
-        "pcot_run": (S, [_VP, _VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+        "pcot_run": (S, [_VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                          ctypes.POINTER(pcot_tile_params), _VP]),
-        "pcot_run_host": (S, [_VP, _VP, _VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                              ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_run_host": (S, [_VP, _VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64, ctypes.c_int,
+                              ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_check": (S, [_VP, _VP]),
         "pcot_plan_query": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
                                 _I32P, _I32P, _I32P, _I64P, _I64P, _I32P, _I32P, ctypes.c_int64]),
@@ -181,16 +181,18 @@ def pcot_workspace_bytes(h, sizes, strides, T, dtype, schedule, params=None):
     return int(n.value)
 
 
-def pcot_run(h, grid, workspace, sizes, strides, T, dtype, schedule, params=None, stream=None):
+def pcot_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule, params=None, stream=None):
     s, st = _i64(sizes), _i64(strides)
-    _chk(_load().pcot_run(h, _ptr(grid), _ptr(workspace), _p64(s), _p64(st), int(T), int(dtype), int(schedule),
-                          _params(params), _stream(stream)), "pcot_run")
+    _chk(_load().pcot_run(h, _ptr(grid), _ptr(workspace), int(workspace_bytes), _p64(s), _p64(st), int(T),
+                          int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_run")
 
 
-def pcot_run_host(h, host_grid, dev_grid, workspace, sizes, strides, T, dtype, schedule, params=None, stream=None):
+def pcot_run_host(h, host_grid, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,
+                  params=None, stream=None):
     s, st = _i64(sizes), _i64(strides)
-    _chk(_load().pcot_run_host(h, _ptr(host_grid), _ptr(dev_grid), _ptr(workspace), _p64(s), _p64(st), int(T),
-                               int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_run_host")
+    _chk(_load().pcot_run_host(h, _ptr(host_grid), _ptr(dev_grid), _ptr(workspace), int(workspace_bytes), _p64(s),
+                               _p64(st), int(T), int(dtype), int(schedule), _params(params), _stream(stream)),
+         "pcot_run_host")
 
 
 def pcot_check(h, stream=None):

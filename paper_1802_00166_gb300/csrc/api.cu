@@ -249,9 +249,9 @@ pcot_status run_blocks(pcot_handle h, const LaunchCtx& L, const pcot_tile_params
     return PCOT_OK;
 }
 
-pcot_status run_impl(pcot_handle h, void* grid, void* workspace, const int64_t* sizes, const int64_t* strides,
-                     int64_t T, pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
-                     void* stream) {
+pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes, const int64_t* sizes,
+                     const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                     const pcot_tile_params* params, void* stream) {
     if (!h || !grid || !workspace || !sizes) return PCOT_ERR_INVALID_ARG;
     if (T < 0) return PCOT_ERR_INVALID_ARG;
     LaunchCtx L;
@@ -260,9 +260,15 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, const int64_t* 
     if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
     if (schedule < PCOT_SWEEP || schedule > PCOT_AUTO) return PCOT_ERR_INVALID_ARG;
     if (T == 0) return PCOT_OK;
-    PCOT_TRY(ensure_device(h));
     if (schedule == PCOT_AUTO) schedule = (L.dtype == kF32 || L.geo.dims == 1) ? PCOT_SLT : PCOT_SWEEP;
     if (schedule == PCOT_COT && L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
+    if (ws_bytes < twin_bytes(L)) return PCOT_ERR_OOM;
+    CotPlanHost* cplan = nullptr;
+    if (schedule == PCOT_COT) {
+        PCOT_TRY(get_cot_plan(h, L, T, params, &cplan));
+        if (ws_bytes < twin_bytes(L) + (cplan->ntiles > 0 ? cplan->image_bytes : 0)) return PCOT_ERR_OOM;
+    }
+    PCOT_TRY(ensure_device(h));
     void* twin = workspace;
     if (!L.geo.periodic) {
         PCOT_CUDA(launch_ring_copy(L, grid, twin));
@@ -297,8 +303,7 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, const int64_t* 
         return PCOT_OK;
     }
     // PCOT_COT
-    CotPlanHost* c = nullptr;
-    PCOT_TRY(get_cot_plan(h, L, T, params, &c));
+    CotPlanHost* c = cplan;
     if (c->ntiles > 0) {
         PCOT_TRY(ensure_image(c));
         unsigned char* ws = (unsigned char*)workspace + twin_bytes(L);
@@ -388,21 +393,21 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t* sizes, const int6
     return PCOT_OK;
 }
 
-pcot_status pcot_run(pcot_handle h, void* grid, void* workspace, const int64_t* sizes, const int64_t* strides,
-                     int64_t T, pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
-                     void* stream) {
-    return run_impl(h, grid, workspace, sizes, strides, T, dtype, schedule, params, stream);
+pcot_status pcot_run(pcot_handle h, void* grid, void* workspace, size_t workspace_bytes, const int64_t* sizes,
+                     const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                     const pcot_tile_params* params, void* stream) {
+    return run_impl(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule, params, stream);
 }
 
-pcot_status pcot_run_host(pcot_handle h, void* host_grid, void* dev_grid, void* workspace, const int64_t* sizes,
-                          const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
-                          const pcot_tile_params* params, void* stream) {
+pcot_status pcot_run_host(pcot_handle h, void* host_grid, void* dev_grid, void* workspace, size_t workspace_bytes,
+                          const int64_t* sizes, const int64_t* strides, int64_t T, pcot_dtype dtype,
+                          pcot_schedule schedule, const pcot_tile_params* params, void* stream) {
     if (!host_grid || !dev_grid) return PCOT_ERR_INVALID_ARG;
     LaunchCtx L;
     PCOT_TRY(make_ctx(h, sizes, strides, dtype, stream, &L));
     const size_t bytes = span_bytes(L);
     PCOT_CUDA(cudaMemcpyAsync(dev_grid, host_grid, bytes, cudaMemcpyHostToDevice, L.stream));
-    PCOT_TRY(run_impl(h, dev_grid, workspace, sizes, strides, T, dtype, schedule, params, stream));
+    PCOT_TRY(run_impl(h, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule, params, stream));
     PCOT_CUDA(cudaMemcpyAsync(host_grid, dev_grid, bytes, cudaMemcpyDeviceToHost, L.stream));
     return pcot_check(h, stream);
 }

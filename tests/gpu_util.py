@@ -49,7 +49,7 @@ def run_gpu(h, grid_np, sizes, T, dtype, schedule, params=None, strides=None, st
     nbytes = pcot.pcot_workspace_bytes(h, sizes, strides, T, dtype, schedule, params)
     ws = torch.empty(nbytes + ws_extra + 256, dtype=torch.uint8, device="cuda")
     ws_ptr = (ws.data_ptr() + 255) // 256 * 256
-    pcot.pcot_run(h, dev.data_ptr(), ws_ptr, sizes, strides, T, dtype, schedule, params, stream)
+    pcot.pcot_run(h, dev.data_ptr(), ws_ptr, nbytes, sizes, strides, T, dtype, schedule, params, stream)
     st = pcot.pcot_check(h, stream)
     if st != pcot.PCOT_OK:
         raise pcot.PcotError(st, "pcot_check")

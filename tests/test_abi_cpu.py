@@ -156,3 +156,19 @@ def test_odd_block_counts_leave_even_tail(lib):
         assert q["lattice"][0] % 2 == 0
         assert q["lattice"][0] * q["depth"] + q["tail_steps"] == T
     pcot.pcot_destroy(h)
+
+
+def test_undersized_workspace_rejected_before_launch(lib):
+    """The size check happens on the host before any device work, so fake
+    (never dereferenced) 256-byte-aligned addresses are enough here."""
+    h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+    sizes = (64, 240)
+    for sched in (pcot.PCOT_SWEEP, pcot.PCOT_SLT, pcot.PCOT_COT):
+        need = pcot.pcot_workspace_bytes(h, sizes, None, 20, pcot.PCOT_F32, sched)
+        with pytest.raises(pcot.PcotError) as e:
+            pcot.pcot_run(h, 1 << 20, 1 << 24, need - 256, sizes, None, 20, pcot.PCOT_F32, sched, None, 0)
+        assert e.value.status == pcot.PCOT_ERR_OOM
+    cot = pcot.pcot_workspace_bytes(h, sizes, None, 20, pcot.PCOT_F32, pcot.PCOT_COT)
+    slt = pcot.pcot_workspace_bytes(h, sizes, None, 20, pcot.PCOT_F32, pcot.PCOT_SLT)
+    assert cot > slt  # the queue image of the recursive schedule lives in the workspace
+    pcot.pcot_destroy(h)

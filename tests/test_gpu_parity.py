@@ -198,7 +198,7 @@ def test_misaligned_workspace_rejected():
     g = torch.zeros((12, 12), dtype=torch.float64, device="cuda")
     ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
     with pytest.raises(pcot.PcotError) as e:
-        pcot.pcot_run(h, g.data_ptr(), ws.data_ptr() + 8, (10, 10), None, 2, pcot.PCOT_F64_EXACT, pcot.PCOT_SLT)
+        pcot.pcot_run(h, g.data_ptr(), ws.data_ptr() + 8, 4000, (10, 10), None, 2, pcot.PCOT_F64_EXACT, pcot.PCOT_SLT)
     assert e.value.status == pcot.PCOT_ERR_ALIGNMENT
     pcot.pcot_destroy(h)
 
@@ -229,7 +229,7 @@ def test_run_host_end_to_end():
     dev = torch.empty_like(host, device="cuda")
     nb = pcot.pcot_workspace_bytes(h, sizes, None, 10, pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    pcot.pcot_run_host(h, host.data_ptr(), dev.data_ptr(), ws.data_ptr(), sizes, None, 10,
+    pcot.pcot_run_host(h, host.data_ptr(), dev.data_ptr(), ws.data_ptr(), nb, sizes, None, 10,
                        pcot.PCOT_F64_EXACT, pcot.PCOT_COT)
     assert np.array_equal(host.numpy(), oracle.sweep(g, sizes, HEAT2D, 10))
     pcot.pcot_destroy(h)
