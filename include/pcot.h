@@ -198,6 +198,129 @@ pcot_status pcot_grid_sum(pcot_handle h, const void *grid, const int64_t *sizes,
                           const int64_t *strides, pcot_dtype dtype, double *out_device,
                           void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched runs: many independent 2-D Dirichlet grids (same stencil, dtype,
+ * time depth and tile width; their own sizes, step counts, tile heights and
+ * recursion thresholds) advanced by ONE persistent kernel.  Each grid's tiles
+ * are ordered by the recursive schedule (Sec. 4.2) of its own lattice; the
+ * per-grid queues are merged so that every grid progresses at the same
+ * relative rate (ties: the grid with more tiles first), which keeps many
+ * independent tiles in flight on all SMs.  The kernel records per-grid
+ * completion times.  The launch sequence (counter reset, ring copy,
+ * persistent kernel) is captured in a CUDA graph by pcot_batch_create and
+ * replayed by pcot_batch_launch.
+ *
+ *  nb        number of grids (1 .. 65535)
+ *  grids     HOST array of nb DEVICE pointers (each grid in/out, layout as for
+ *            pcot_run; the result lands in the caller's grid)
+ *  sizes     nb*2 interior sizes (row-major per grid)
+ *  strides   nb*2 element strides, or NULL for contiguous grids
+ *  T         nb step counts (>= 0)
+ *  params    nb tile parameter sets or NULL; time_depth (1, 2, 4 or 8 for
+ *            PCOT_F32; 1, 2 or 4 otherwise) and tile[1] (warps per tile via
+ *            the tile width) are taken from params[0] for all grids; tile[0]
+ *            and cot_threshold per grid
+ *  workspace device scratch of pcot_batch_workspace_bytes bytes (queue,
+ *            counters, descriptors and one twin per grid), 256-byte aligned;
+ *            it must stay allocated and untouched while the batch exists
+ *  done_ns   DEVICE array of nb+1 uint64 or NULL: [0] receives the
+ *            %globaltimer (ns) when the first tile starts, [1+g] when grid g's
+ *            last tile finished (latency of grid g = done_ns[1+g]-done_ns[0])
+ * ------------------------------------------------------------------------ */
+typedef struct pcot_batch_s *pcot_batch;
+
+pcot_status pcot_batch_workspace_bytes(pcot_handle h, int nb, const int64_t *sizes,
+                                       const int64_t *strides, const int64_t *T, pcot_dtype dtype,
+                                       const pcot_tile_params *params, size_t *bytes);
+
+pcot_status pcot_batch_create(pcot_handle h, int nb, void *const *grids, const int64_t *sizes,
+                              const int64_t *strides, const int64_t *T, pcot_dtype dtype,
+                              const pcot_tile_params *params, void *workspace,
+                              size_t workspace_bytes, uint64_t *done_ns, void *stream,
+                              pcot_batch *out);
+
+/* Replay the captured graph on `stream` (asynchronous; pcot_check reports
+ * device-side errors). */
+pcot_status pcot_batch_launch(pcot_batch b, void *stream);
+
+/* Release the graph and host plan (call after the last launch completed). */
+pcot_status pcot_batch_destroy(pcot_batch b);
+
+/* create + launch + synchronise + destroy; returns the pcot_check status. */
+pcot_status pcot_run_batched(pcot_handle h, int nb, void *const *grids, const int64_t *sizes,
+                             const int64_t *strides, const int64_t *T, pcot_dtype dtype,
+                             const pcot_tile_params *params, void *workspace,
+                             size_t workspace_bytes, uint64_t *done_ns, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Exhaustive autotuner (the GPU counterpart of the tile-size exploration of
+ * Sec. 5.1.5: every candidate timed, mean over repetitions).
+ *  grid, workspace  as for pcot_run; the workspace must be large enough for
+ *             every candidate (pcot_workspace_bytes of the largest); the grid
+ *             CONTENTS ARE ADVANCED by the timing runs (use a scratch copy)
+ *  ncand      number of candidates; schedules[i] and params[i] describe one
+ *  reps       timed repetitions per candidate (after one untimed warm-up)
+ *  ms_out     HOST array of ncand floats: mean milliseconds of one pcot_run,
+ *             or -1 for a candidate the library rejects (unsupported shape,
+ *             workspace too small)
+ * Synchronous: returns after the last timing.
+ * ------------------------------------------------------------------------ */
+pcot_status pcot_autotune(pcot_handle h, void *grid, void *workspace, size_t workspace_bytes,
+                          const int64_t *sizes, const int64_t *strides, int64_t T, pcot_dtype dtype,
+                          int ncand, const pcot_schedule *schedules, const pcot_tile_params *params,
+                          int reps, float *ms_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned tile picker.  A 12-64-64-64-2 ReLU MLP (FP32, 9282 parameters in
+ * one flat array: W1 (64x12, row = output), b1, W2 (64x64), b2, W3, b3,
+ * W4 (2x64), b4) maps a normalised feature vector of (problem, schedule,
+ * tile parameters) to (log milliseconds, log modelled HBM bytes).  Training
+ * and inference run in the library's kernels; all pointers are DEVICE
+ * pointers unless stated.  x is batch x 12, y and targets batch x 2, all
+ * row-major.
+ * ------------------------------------------------------------------------ */
+int pcot_mlp_param_count(void);
+
+/* Device scratch needed by pcot_mlp_grad for a batch. */
+pcot_status pcot_mlp_scratch_bytes(int batch, size_t *bytes);
+
+pcot_status pcot_mlp_forward(const float *params, const float *x, int batch, float *y, void *stream);
+
+/* Gradient of L = (1/batch) sum 0.5 (y - target)^2 into grad (9282 floats)
+ * and L into *loss (device, may be NULL); deterministic reduction order. */
+pcot_status pcot_mlp_grad(const float *params, const float *x, const float *target, int batch,
+                          float *grad, float *loss, void *scratch, size_t scratch_bytes,
+                          void *stream);
+
+/* One Adam step (Kingma and Ba) with bias correction; step counts from 1. */
+pcot_status pcot_mlp_adam(float *params, const float *grad, float *m, float *v, int n, int step,
+                          float lr, float beta1, float beta2, float eps, void *stream);
+
+/* *out_index (device int) = argmin over rows of y[row * stride + col]. */
+pcot_status pcot_mlp_argmin(const float *y, int n, int stride, int col, int *out_index, void *stream);
+
+/*
+ * Feature vector (12 floats, HOST) of one candidate, before normalisation:
+ * [dims, radius, log2 n_0, log2 n_1, log2 n_2 (0 when absent), log2 T,
+ *  log2 tile_0, log2 tile_1, log2 tile_2 (extents actually used; the grid
+ *  extents for the sweep), log2 k (0 for the sweep), log2 of the leaf
+ *  orthant volume in tiles (PCOT_COT) or -1 (sweep / single-level), dtype].
+ */
+pcot_status pcot_features(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
+                          pcot_schedule schedule, const pcot_tile_params *params, float *out12);
+
+/*
+ * Pick the candidate with the least predicted time: builds the features of
+ * the ncand candidates, normalises them with mean/std (HOST, 12 + 12
+ * floats), runs the MLP forward and argmin kernels, returns the index in
+ * *best (HOST).  `scratch` is device memory of at least
+ * ncand * (12 + 2) * 4 + 256 bytes.  Synchronous.
+ */
+pcot_status pcot_pick(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
+                      const float *mlp_params, const float *feat_mean, const float *feat_std,
+                      int ncand, const pcot_schedule *schedules, const pcot_tile_params *params,
+                      void *scratch, int *best, void *stream);
+
 /*
  * Number of kernels this handle has launched since it was created (sweep
  * steps, single-level blocks, persistent executors, ring copies, sums).

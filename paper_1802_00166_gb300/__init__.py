@@ -93,6 +93,30 @@ def _load():
         "pcot_test_wait_timeout": (S, [_VP, _VP, ctypes.c_int32, _VP]),
         "pcot_grid_sum": (S, [_VP, _VP, _I64P, _I64P, ctypes.c_int, _VP, _VP]),
         "pcot_launch_count": (S, [_VP, _I64P]),
+        "pcot_batch_workspace_bytes": (S, [_VP, ctypes.c_int, _I64P, _I64P, _I64P, ctypes.c_int,
+                                           ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_batch_create": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP), _I64P, _I64P, _I64P, ctypes.c_int,
+                                  ctypes.POINTER(pcot_tile_params), _VP, ctypes.c_size_t, _VP, _VP,
+                                  ctypes.POINTER(_VP)]),
+        "pcot_batch_launch": (S, [_VP, _VP]),
+        "pcot_batch_destroy": (S, [_VP]),
+        "pcot_run_batched": (S, [_VP, ctypes.c_int, ctypes.POINTER(_VP), _I64P, _I64P, _I64P, ctypes.c_int,
+                                 ctypes.POINTER(pcot_tile_params), _VP, ctypes.c_size_t, _VP, _VP]),
+        "pcot_autotune": (S, [_VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(pcot_tile_params), ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_float), _VP]),
+        "pcot_mlp_param_count": (ctypes.c_int, []),
+        "pcot_mlp_scratch_bytes": (S, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_mlp_forward": (S, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+        "pcot_mlp_grad": (S, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+        "pcot_mlp_adam": (S, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, _VP]),
+        "pcot_mlp_argmin": (S, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+        "pcot_features": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
+                              ctypes.POINTER(ctypes.c_float)]),
+        "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
+                          ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -106,7 +130,10 @@ def exported_symbols():
     """Names declared in include/pcot.h that this binding marshals."""
     return ["pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
             "pcot_run_host", "pcot_check", "pcot_plan_query", "pcot_test_wait_timeout", "pcot_grid_sum",
-            "pcot_launch_count"]
+            "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
+            "pcot_batch_destroy", "pcot_run_batched", "pcot_autotune", "pcot_mlp_param_count",
+            "pcot_mlp_scratch_bytes", "pcot_mlp_forward", "pcot_mlp_grad", "pcot_mlp_adam", "pcot_mlp_argmin",
+            "pcot_features", "pcot_pick"]
 
 
 def status_string(s):
@@ -236,6 +263,121 @@ def pcot_launch_count(h):
     n = ctypes.c_int64()
     _chk(_load().pcot_launch_count(h, ctypes.byref(n)), "pcot_launch_count")
     return int(n.value)
+
+
+def _param_array(params, nb):
+    if params is None:
+        return None
+    arr = (pcot_tile_params * nb)()
+    for i, p in enumerate(params):
+        arr[i] = p if isinstance(p, pcot_tile_params) else tile_params(**p)
+    return arr
+
+
+def _ptr_array(ptrs):
+    arr = (_VP * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = _ptr(p)
+    return arr
+
+
+def pcot_batch_workspace_bytes(h, sizes, strides, T, dtype, params=None):
+    nb = len(T)
+    n = ctypes.c_size_t()
+    _chk(_load().pcot_batch_workspace_bytes(h, nb, _p64(_i64(sizes)), _p64(_i64(strides)), _p64(_i64(T)), int(dtype),
+                                            _param_array(params, nb), ctypes.byref(n)), "pcot_batch_workspace_bytes")
+    return int(n.value)
+
+
+def pcot_batch_create(h, grids, sizes, strides, T, dtype, params, workspace, workspace_bytes, done_ns=None,
+                      stream=None):
+    nb = len(grids)
+    b = _VP()
+    _chk(_load().pcot_batch_create(h, nb, _ptr_array(grids), _p64(_i64(sizes)), _p64(_i64(strides)), _p64(_i64(T)),
+                                   int(dtype), _param_array(params, nb), _ptr(workspace), int(workspace_bytes),
+                                   _ptr(done_ns), _stream(stream), ctypes.byref(b)), "pcot_batch_create")
+    return b
+
+
+def pcot_batch_launch(b, stream=None):
+    _chk(_load().pcot_batch_launch(b, _stream(stream)), "pcot_batch_launch")
+
+
+def pcot_batch_destroy(b):
+    _chk(_load().pcot_batch_destroy(b), "pcot_batch_destroy")
+
+
+def pcot_run_batched(h, grids, sizes, strides, T, dtype, params, workspace, workspace_bytes, done_ns=None,
+                     stream=None):
+    nb = len(grids)
+    _chk(_load().pcot_run_batched(h, nb, _ptr_array(grids), _p64(_i64(sizes)), _p64(_i64(strides)), _p64(_i64(T)),
+                                  int(dtype), _param_array(params, nb), _ptr(workspace), int(workspace_bytes),
+                                  _ptr(done_ns), _stream(stream)), "pcot_run_batched")
+
+
+def _sched_array(scheds):
+    arr = (ctypes.c_int * len(scheds))()
+    for i, v in enumerate(scheds):
+        arr[i] = int(v)
+    return arr
+
+
+def pcot_autotune(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedules, params, reps=2,
+                  stream=None):
+    """Mean milliseconds per candidate (-1 where the library rejects it)."""
+    n = len(schedules)
+    out = (ctypes.c_float * n)()
+    _chk(_load().pcot_autotune(h, _ptr(grid), _ptr(workspace), int(workspace_bytes), _p64(_i64(sizes)),
+                               _p64(_i64(strides)), int(T), int(dtype), n, _sched_array(schedules),
+                               _param_array(params, n), int(reps), out, _stream(stream)), "pcot_autotune")
+    return [float(v) for v in out]
+
+
+def pcot_mlp_param_count():
+    return int(_load().pcot_mlp_param_count())
+
+
+def pcot_mlp_scratch_bytes(batch):
+    n = ctypes.c_size_t()
+    _chk(_load().pcot_mlp_scratch_bytes(int(batch), ctypes.byref(n)), "pcot_mlp_scratch_bytes")
+    return int(n.value)
+
+
+def pcot_mlp_forward(params, x, batch, y, stream=None):
+    _chk(_load().pcot_mlp_forward(_ptr(params), _ptr(x), int(batch), _ptr(y), _stream(stream)), "pcot_mlp_forward")
+
+
+def pcot_mlp_grad(params, x, target, batch, grad, loss, scratch, scratch_bytes, stream=None):
+    _chk(_load().pcot_mlp_grad(_ptr(params), _ptr(x), _ptr(target), int(batch), _ptr(grad), _ptr(loss),
+                               _ptr(scratch), int(scratch_bytes), _stream(stream)), "pcot_mlp_grad")
+
+
+def pcot_mlp_adam(params, grad, m, v, n, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _chk(_load().pcot_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(n), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _stream(stream)), "pcot_mlp_adam")
+
+
+def pcot_mlp_argmin(y, n, stride, col, out_index, stream=None):
+    _chk(_load().pcot_mlp_argmin(_ptr(y), int(n), int(stride), int(col), _ptr(out_index), _stream(stream)),
+         "pcot_mlp_argmin")
+
+
+def pcot_features(h, sizes, T, dtype, schedule, params=None):
+    out = (ctypes.c_float * 12)()
+    _chk(_load().pcot_features(h, _p64(_i64(sizes)), int(T), int(dtype), int(schedule), _params(params), out),
+         "pcot_features")
+    return np.array(list(out), dtype=np.float32)
+
+
+def pcot_pick(h, sizes, T, dtype, mlp_params, feat_mean, feat_std, schedules, params, scratch, stream=None):
+    n = len(schedules)
+    mean = (ctypes.c_float * 12)(*[float(v) for v in feat_mean])
+    std = (ctypes.c_float * 12)(*[float(v) for v in feat_std])
+    best = ctypes.c_int(-1)
+    _chk(_load().pcot_pick(h, _p64(_i64(sizes)), int(T), int(dtype), _ptr(mlp_params), mean, std, n,
+                           _sched_array(schedules), _param_array(params, n), _ptr(scratch), ctypes.byref(best),
+                           _stream(stream)), "pcot_pick")
+    return int(best.value)
 
 
 def library_path():

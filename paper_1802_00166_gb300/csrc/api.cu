@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -482,6 +483,479 @@ pcot_status pcot_grid_sum(pcot_handle h, const void* grid, const int64_t* sizes,
 pcot_status pcot_launch_count(pcot_handle h, int64_t* launches) {
     if (!h || !launches) return PCOT_ERR_INVALID_ARG;
     *launches = h->launches;
+    return PCOT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched runs
+// ---------------------------------------------------------------------------
+#include <queue>
+
+#include "tiled.cuh"
+
+namespace {
+
+struct BatchPlanHost {
+    int nb = 0, dtype = 0, depth = 0, nwarps = 1;
+    std::vector<LaunchCtx> ctx;
+    std::vector<TileGeo> tg;
+    std::vector<int32_t> Pmain, Ptotal, base, ntiles, final_copy;
+    bool any_final_copy = false;
+    std::vector<int2> queue;
+    std::vector<int32_t> counts;  // initial values, by global counter index
+    std::vector<int32_t> remaining;
+    // workspace layout
+    size_t off_desc = 0, off_queue = 0, off_counts = 0, off_counts0 = 0, off_rem = 0, off_rem0 = 0, off_head = 0;
+    std::vector<size_t> off_twin;
+    size_t total = 0;
+};
+
+pcot_status build_batch_plan(pcot_handle h, int nb, const int64_t* sizes, const int64_t* strides, const int64_t* T,
+                             pcot_dtype dtype, const pcot_tile_params* params, BatchPlanHost* B) {
+    if (!h || nb < 1 || nb > 65535 || !sizes || !T) return PCOT_ERR_INVALID_ARG;
+    if (h->dims != 2 || h->boundary != PCOT_DIRICHLET) return PCOT_ERR_UNSUPPORTED;
+    B->nb = nb;
+    B->dtype = (int)dtype;
+    const int kdef = dtype == PCOT_F32 ? 8 : 2;
+    B->depth = params && params[0].time_depth > 0 ? params[0].time_depth : kdef;
+    const int d = B->depth;
+    if (!(d == 1 || d == 2 || d == 4 || (d == 8 && dtype == PCOT_F32))) return PCOT_ERR_UNSUPPORTED;
+    const int E = dtype == PCOT_F32 ? 4 : 2;
+    const int Kp = ((d + E - 1) / E) * E;
+    const int Wo = 32 * E - 2 * Kp;
+    B->nwarps = params && params[0].tile[1] > 0 ? (int)std::max<int64_t>(1, (params[0].tile[1] + Wo / 2) / Wo) : 1;
+    B->ctx.resize(nb);
+    B->tg.resize(nb);
+    B->Pmain.resize(nb);
+    B->Ptotal.resize(nb);
+    B->base.resize(nb);
+    B->ntiles.resize(nb);
+    B->final_copy.assign(nb, 0);
+    std::vector<std::vector<int32_t>> qs(nb);
+    int64_t total = 0;
+    for (int g = 0; g < nb; ++g) {
+        if (T[g] < 0) return PCOT_ERR_INVALID_ARG;
+        PCOT_TRY(make_ctx(h, sizes + 2 * g, strides ? strides + 2 * g : nullptr, dtype, nullptr, &B->ctx[g]));
+        const int64_t H = params && params[g].tile[0] > 0 ? params[g].tile[0] : 64;
+        if (!stream2d::batch_tiles(B->ctx[g], d, B->nwarps, H, &B->tg[g])) return PCOT_ERR_UNSUPPORTED;
+        int64_t Pm = T[g] / d, tail = T[g] - Pm * d;
+        if ((Pm + tail) % 2 == 1) {
+            if (Pm > 0) {
+                Pm -= 1;
+                tail += d;
+            } else {
+                B->final_copy[g] = 1;  // odd T below the depth: the result is copied back at the end
+                B->any_final_copy = true;
+            }
+        }
+        if (Pm + tail > (1 << 20)) return PCOT_ERR_UNSUPPORTED;
+        B->Pmain[g] = (int32_t)Pm;
+        B->Ptotal[g] = (int32_t)(Pm + tail);
+        const int64_t Lax[3] = {B->tg[g].count[0], B->tg[g].count[1], 1};
+        const int64_t n = (int64_t)B->Ptotal[g] * Lax[0] * Lax[1];
+        if (total + n > 0x7fffffffLL) return PCOT_ERR_UNSUPPORTED;
+        B->base[g] = (int32_t)total;
+        B->ntiles[g] = (int32_t)n;
+        total += n;
+        if (n > 0) {
+            int64_t theta[4] = {2, 8, 8, 1};
+            if (params)
+                for (int i = 0; i < 3; ++i)
+                    if (params[g].cot_threshold[i] > 0) theta[i] = params[g].cot_threshold[i];
+            qs[g] = pcot_lattice_order(B->Ptotal[g], 2, Lax, theta, nullptr);
+            std::vector<int32_t> c = lattice_dep_counts(B->Ptotal[g], 2, Lax);
+            B->counts.insert(B->counts.end(), c.begin(), c.end());
+        }
+    }
+    // Merge: the grid whose next tile sits earliest in its own queue
+    // (relative position) goes next; ties go to the grid with more tiles.
+    struct Key {
+        double frac;
+        int32_t len;
+        int g;
+        bool operator<(const Key& o) const {
+            if (frac != o.frac) return frac > o.frac;
+            if (len != o.len) return len < o.len;
+            return g > o.g;
+        }
+    };
+    std::priority_queue<Key> pq;
+    std::vector<size_t> pos(nb, 0);
+    for (int g = 0; g < nb; ++g)
+        if (!qs[g].empty()) pq.push({1.0 / (double)qs[g].size(), (int32_t)qs[g].size(), g});
+    B->queue.reserve((size_t)total);
+    while (!pq.empty()) {
+        Key k = pq.top();
+        pq.pop();
+        const int g = k.g;
+        B->queue.push_back(make_int2(g, qs[g][pos[g]]));
+        if (++pos[g] < qs[g].size())
+            pq.push({(double)(pos[g] + 1) / (double)qs[g].size(), (int32_t)qs[g].size(), g});
+    }
+    B->remaining.assign(B->ntiles.begin(), B->ntiles.end());
+    // Workspace layout.
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = round_up(o + bytes, kAlign);
+        return at;
+    };
+    B->off_desc = take(sizeof(BatchDesc) * (size_t)nb);
+    B->off_queue = take(sizeof(int2) * (size_t)std::max<int64_t>(total, 1));
+    B->off_counts = take(sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1));
+    B->off_counts0 = take(sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1));
+    B->off_rem = take(sizeof(int32_t) * (size_t)nb);
+    B->off_rem0 = take(sizeof(int32_t) * (size_t)nb);
+    B->off_head = take(sizeof(int32_t));
+    B->off_twin.resize(nb);
+    for (int g = 0; g < nb; ++g) B->off_twin[g] = take(span_bytes(B->ctx[g]));
+    B->total = o;
+    return PCOT_OK;
+}
+
+}  // namespace
+
+struct pcot_batch_s {
+    pcot_handle h = nullptr;
+    BatchPlanHost plan;
+    BatchDev dev{};
+    int nctas = 1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+pcot_status pcot_batch_workspace_bytes(pcot_handle h, int nb, const int64_t* sizes, const int64_t* strides,
+                                       const int64_t* T, pcot_dtype dtype, const pcot_tile_params* params,
+                                       size_t* bytes) {
+    if (!bytes) return PCOT_ERR_INVALID_ARG;
+    BatchPlanHost B;
+    PCOT_TRY(build_batch_plan(h, nb, sizes, strides, T, dtype, params, &B));
+    *bytes = B.total;
+    return PCOT_OK;
+}
+
+pcot_status pcot_batch_create(pcot_handle h, int nb, void* const* grids, const int64_t* sizes, const int64_t* strides,
+                              const int64_t* T, pcot_dtype dtype, const pcot_tile_params* params, void* workspace,
+                              size_t workspace_bytes, uint64_t* done_ns, void* stream, pcot_batch* out) {
+    if (!out || !grids || !workspace) return PCOT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
+    pcot_batch_s* b = new pcot_batch_s();
+    b->h = h;
+    pcot_status st = build_batch_plan(h, nb, sizes, strides, T, dtype, params, &b->plan);
+    if (st == PCOT_OK && workspace_bytes < b->plan.total) st = PCOT_ERR_OOM;
+    if (st == PCOT_OK) st = ensure_device(h);
+    if (st != PCOT_OK) {
+        delete b;
+        return st;
+    }
+    BatchPlanHost& P = b->plan;
+    unsigned char* ws = (unsigned char*)workspace;
+    std::vector<BatchDesc> desc((size_t)nb);
+    BatchDev& q = b->dev;
+    q.nbox = 1;
+    q.BW = 32;
+    q.box_elems = 128;
+    q.slot_elems = 128;
+    q.all_tma = 1;
+    for (int g = 0; g < nb; ++g) {
+        BatchDesc& d = desc[g];
+        std::memset(&d, 0, sizeof(d));
+        if (!grids[g] || ((uintptr_t)grids[g] % elem_size(dtype)) != 0) {
+            delete b;
+            return grids[g] ? PCOT_ERR_ALIGNMENT : PCOT_ERR_INVALID_ARG;
+        }
+        d.buf[0] = grids[g];
+        d.buf[1] = ws + P.off_twin[g];
+        d.g = P.ctx[g].geo;
+        d.H = P.tg[g].ext[0];
+        d.Wt = P.tg[g].ext[1];
+        d.L0 = (int32_t)P.tg[g].count[0];
+        d.L1 = (int32_t)P.tg[g].count[1];
+        d.Pmain = P.Pmain[g];
+        d.Ptotal = P.Ptotal[g];
+        d.count_base = P.base[g];
+        d.ntiles = P.ntiles[g];
+        d.final_copy = P.final_copy[g];
+        d.span = (int64_t)(span_bytes(P.ctx[g]) / elem_size(dtype));
+        const int es = elem_size(dtype);
+        d.vec_ok = (((uintptr_t)d.buf[0] & 15) == 0 && ((uintptr_t)d.buf[1] & 15) == 0 &&
+                    ((d.g.s[0] * es) & 15) == 0)
+                       ? 1
+                       : 0;
+        BatchDev ring{};
+        if (stream2d::batch_desc_tma(P.ctx[g], P.tg[g], &d, &ring)) {
+            q.nbox = ring.nbox;
+            q.BW = ring.BW;
+            q.box_elems = ring.box_elems;
+            q.slot_elems = ring.slot_elems;
+        } else {
+            q.all_tma = 0;
+        }
+    }
+    const int64_t total = (int64_t)P.queue.size();
+    q.desc = (const BatchDesc*)(ws + P.off_desc);
+    q.queue = (const int2*)(ws + P.off_queue);
+    q.counts = (int32_t*)(ws + P.off_counts);
+    q.remaining = (int32_t*)(ws + P.off_rem);
+    q.head = (int32_t*)(ws + P.off_head);
+    q.ntiles = total;
+    q.done_ns = done_ns;
+    q.status = h->d_status;
+    q.timeout_ns = h->timeout_ns;
+    q.nb = nb;
+    // One-time upload of descriptors, queue and initial counters.
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ws + P.off_desc, desc.data(), sizeof(BatchDesc) * desc.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && total > 0)
+        e = cudaMemcpyAsync(ws + P.off_queue, P.queue.data(), sizeof(int2) * (size_t)total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && total > 0)
+        e = cudaMemcpyAsync(ws + P.off_counts0, P.counts.data(), sizeof(int32_t) * (size_t)total,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + P.off_rem0, P.remaining.data(), sizeof(int32_t) * (size_t)nb, cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int per_sm = stream2d::batch_ctas_per_sm(P.dtype, P.depth, P.nwarps, q);
+    int64_t nctas = (int64_t)per_sm * h->num_sms;
+    if (nctas > total) nctas = total;
+    b->nctas = (int)std::max<int64_t>(1, nctas);
+    // Capture: counter reset, ring copy, persistent kernel.
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ce = cudaSuccess;
+        if (total > 0)
+            ce = cudaMemcpyAsync(ws + P.off_counts, ws + P.off_counts0, sizeof(int32_t) * (size_t)total,
+                                 cudaMemcpyDeviceToDevice, cs);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(ws + P.off_rem, ws + P.off_rem0, sizeof(int32_t) * (size_t)nb,
+                                 cudaMemcpyDeviceToDevice, cs);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(ws + P.off_head, 0, sizeof(int32_t), cs);
+        if (ce == cudaSuccess) ce = stream2d::batch_ring_copy(P.dtype, q, cs);
+        if (ce == cudaSuccess && total > 0)
+            ce = stream2d::batch_launch(P.dtype, P.depth, P.nwarps, h->coeffs, q, b->nctas, cs);
+        if (ce == cudaSuccess && P.any_final_copy) ce = stream2d::batch_final_copy(P.dtype, q, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return from_cuda(e);
+    }
+    *out = b;
+    return PCOT_OK;
+}
+
+pcot_status pcot_batch_launch(pcot_batch b, void* stream) {
+    if (!b) return PCOT_ERR_INVALID_ARG;
+    PCOT_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    b->h->launches += 1 + (b->dev.ntiles > 0 ? 1 : 0) + (b->plan.any_final_copy ? 1 : 0);
+    return PCOT_OK;
+}
+
+pcot_status pcot_batch_destroy(pcot_batch b) {
+    if (!b) return PCOT_ERR_INVALID_ARG;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    return PCOT_OK;
+}
+
+pcot_status pcot_run_batched(pcot_handle h, int nb, void* const* grids, const int64_t* sizes, const int64_t* strides,
+                             const int64_t* T, pcot_dtype dtype, const pcot_tile_params* params, void* workspace,
+                             size_t workspace_bytes, uint64_t* done_ns, void* stream) {
+    pcot_batch b = nullptr;
+    PCOT_TRY(pcot_batch_create(h, nb, grids, sizes, strides, T, dtype, params, workspace, workspace_bytes, done_ns,
+                               stream, &b));
+    pcot_status st = pcot_batch_launch(b, stream);
+    const pcot_status ck = pcot_check(h, stream);
+    pcot_batch_destroy(b);
+    return st != PCOT_OK ? st : ck;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------
+extern "C" pcot_status pcot_autotune(pcot_handle h, void* grid, void* workspace, size_t workspace_bytes,
+                                     const int64_t* sizes, const int64_t* strides, int64_t T, pcot_dtype dtype,
+                                     int ncand, const pcot_schedule* schedules, const pcot_tile_params* params,
+                                     int reps, float* ms_out, void* stream) {
+    if (!h || !grid || !workspace || !sizes || ncand < 1 || !schedules || !ms_out || reps < 1) return PCOT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PCOT_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return from_cuda(ce);
+    }
+    pcot_status result = PCOT_OK;
+    for (int i = 0; i < ncand; ++i) {
+        ms_out[i] = -1.0f;
+        const pcot_tile_params* p = params ? &params[i] : nullptr;
+        pcot_status st = pcot_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedules[i], p,
+                                  stream);
+        if (st == PCOT_ERR_UNSUPPORTED || st == PCOT_ERR_OOM) continue;
+        if (st != PCOT_OK) {
+            result = st;
+            break;
+        }
+        ce = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && ce == cudaSuccess && st == PCOT_OK; ++r)
+            st = pcot_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedules[i], p, stream);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess || st != PCOT_OK) {
+            result = ce != cudaSuccess ? from_cuda(ce) : st;
+            break;
+        }
+        const pcot_status ck = pcot_check(h, stream);
+        if (ck != PCOT_OK) {
+            result = ck;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_out[i] = ms / (float)reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
+}
+
+// ---------------------------------------------------------------------------
+// Learned tile picker
+// ---------------------------------------------------------------------------
+namespace {
+
+float log2f_safe(double v) { return v > 0 ? (float)std::log2(v) : 0.f; }
+
+pcot_status features_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                          const pcot_tile_params* p, float* f) {
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, nullptr, dtype, nullptr, &L));
+    for (int i = 0; i < 12; ++i) f[i] = 0.f;
+    f[0] = (float)L.geo.dims;
+    f[1] = (float)h->radius;
+    for (int a = 0; a < L.geo.dims; ++a) f[2 + a] = log2f_safe((double)L.geo.n[a]);
+    f[5] = log2f_safe((double)std::max<int64_t>(T, 1));
+    f[11] = (float)dtype;
+    if (schedule == PCOT_SWEEP) {
+        for (int a = 0; a < L.geo.dims; ++a) f[6 + a] = log2f_safe((double)L.geo.e[a]);
+        f[9] = 0.f;
+        f[10] = -1.f;
+        return PCOT_OK;
+    }
+    int k = p && p->time_depth > 0 ? p->time_depth : default_depth(L);
+    TileGeo tg;
+    if (!choose_tiles(L, p ? p->tile : nullptr, k, &tg)) return PCOT_ERR_UNSUPPORTED;
+    for (int a = 0; a < L.geo.dims; ++a) f[6 + a] = log2f_safe((double)tg.ext[a]);
+    f[9] = log2f_safe((double)k);
+    if (schedule == PCOT_COT) {
+        double vol = 1.0;
+        for (int i = 0; i <= L.geo.dims; ++i) vol *= (p && p->cot_threshold[i] > 0) ? p->cot_threshold[i] : 1;
+        f[10] = log2f_safe(vol);
+    } else {
+        f[10] = -1.f;
+    }
+    return PCOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcot_mlp_param_count(void) { return mlp::param_count(); }
+
+pcot_status pcot_mlp_scratch_bytes(int batch, size_t* bytes) {
+    if (batch < 1 || !bytes) return PCOT_ERR_INVALID_ARG;
+    *bytes = mlp::scratch_bytes(batch);
+    return PCOT_OK;
+}
+
+pcot_status pcot_mlp_forward(const float* params, const float* x, int batch, float* y, void* stream) {
+    if (!params || !x || !y || batch < 1) return PCOT_ERR_INVALID_ARG;
+    PCOT_CUDA(mlp::forward(params, x, batch, y, (cudaStream_t)stream));
+    return PCOT_OK;
+}
+
+pcot_status pcot_mlp_grad(const float* params, const float* x, const float* target, int batch, float* grad,
+                          float* loss, void* scratch, size_t scratch_bytes, void* stream) {
+    if (!params || !x || !target || !grad || !scratch || batch < 1) return PCOT_ERR_INVALID_ARG;
+    if (scratch_bytes < mlp::scratch_bytes(batch)) return PCOT_ERR_OOM;
+    if (((uintptr_t)scratch & 15) != 0) return PCOT_ERR_ALIGNMENT;
+    PCOT_CUDA(mlp::grad(params, x, target, batch, grad, loss, scratch, (cudaStream_t)stream));
+    return PCOT_OK;
+}
+
+pcot_status pcot_mlp_adam(float* params, const float* grad, float* m, float* v, int n, int step, float lr,
+                          float beta1, float beta2, float eps, void* stream) {
+    if (!params || !grad || !m || !v || n < 1 || step < 1) return PCOT_ERR_INVALID_ARG;
+    PCOT_CUDA(mlp::adam(params, grad, m, v, n, step, lr, beta1, beta2, eps, (cudaStream_t)stream));
+    return PCOT_OK;
+}
+
+pcot_status pcot_mlp_argmin(const float* y, int n, int stride, int col, int* out_index, void* stream) {
+    if (!y || !out_index || n < 1 || stride < 1 || col < 0 || col >= stride) return PCOT_ERR_INVALID_ARG;
+    PCOT_CUDA(mlp::argmin(y, n, stride, col, out_index, (cudaStream_t)stream));
+    return PCOT_OK;
+}
+
+pcot_status pcot_features(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                          const pcot_tile_params* params, float* out12) {
+    if (!h || !sizes || !out12 || T < 0) return PCOT_ERR_INVALID_ARG;
+    return features_impl(h, sizes, T, dtype, schedule, params, out12);
+}
+
+pcot_status pcot_pick(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, const float* mlp_params,
+                      const float* feat_mean, const float* feat_std, int ncand, const pcot_schedule* schedules,
+                      const pcot_tile_params* params, void* scratch, int* best, void* stream) {
+    if (!h || !sizes || !mlp_params || !feat_mean || !feat_std || ncand < 1 || !schedules || !scratch || !best)
+        return PCOT_ERR_INVALID_ARG;
+    std::vector<float> x((size_t)ncand * 12);
+    std::vector<int> ok((size_t)ncand, 1);
+    for (int i = 0; i < ncand; ++i) {
+        float f[12];
+        if (features_impl(h, sizes, T, dtype, schedules[i], params ? &params[i] : nullptr, f) != PCOT_OK) {
+            ok[i] = 0;
+            for (int j = 0; j < 12; ++j) f[j] = 0.f;
+        }
+        for (int j = 0; j < 12; ++j) {
+            const float sd = feat_std[j] > 0.f ? feat_std[j] : 1.f;
+            x[(size_t)i * 12 + j] = (f[j] - feat_mean[j]) / sd;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* dx = (float*)scratch;
+    float* dy = dx + (size_t)ncand * 12;
+    int* didx = (int*)(dy + (size_t)ncand * 2);
+    PCOT_CUDA(cudaMemcpyAsync(dx, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    PCOT_CUDA(mlp::forward(mlp_params, dx, ncand, dy, s));
+    // Unsupported candidates must never win: overwrite their prediction.
+    for (int i = 0; i < ncand; ++i)
+        if (!ok[i]) {
+            const float big = 1e30f;
+            PCOT_CUDA(cudaMemcpyAsync(dy + (size_t)i * 2, &big, sizeof(float), cudaMemcpyHostToDevice, s));
+        }
+    PCOT_CUDA(mlp::argmin(dy, ncand, 2, 0, didx, s));
+    int idx = -1;
+    PCOT_CUDA(cudaMemcpyAsync(&idx, didx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PCOT_CUDA(cudaStreamSynchronize(s));
+    if (idx < 0 || idx >= ncand) return PCOT_ERR_CUDA;
+    *best = idx;
     return PCOT_OK;
 }
 

@@ -20,6 +20,7 @@
 //    lane issues the copies).  Out-of-grid cells arrive as zeros.
 //  * plain loads (periodic grids, layouts without 16-byte rows): each lane
 //    keeps three rows of 16-byte loads in flight in registers.
+#include <algorithm>
 #include <cstring>
 
 #include "tiled.cuh"
@@ -530,7 +531,182 @@ int occ_k(const LaunchCtx& L, const TileGeo& t) {
     return n > 0 ? n : 1;
 }
 
+
+// Persistent kernel over the merged tile queue of a batch of grids.
+template <class T, bool EXACT, int K, bool TMA>
+__global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeffs<T> c) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int E = Vec<T>::E;
+    constexpr int Wo = Shape<K, E>::Wo;
+    constexpr int Kp = Shape<K, E>::Kp;
+    __shared__ int s_g, s_local, s_pos;
+    const int nwarps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    Args<T> A{};
+    A.c = c;
+    A.st = q.status;
+    A.timeout_ns = q.timeout_ns;
+    A.nbox = q.nbox;
+    A.BW = q.BW;
+    A.box_elems = q.box_elems;
+    A.slot_elems = q.slot_elems;
+    const SmemRing<T> r = carve<T>(smraw, A);
+    init_ring(r, nwarps);
+    uint32_t fill_base = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int pos = atomicAdd(q.head, 1);
+            int g = -1, local = 0;
+            if (pos < q.ntiles) {
+                if (pos == 0 && q.done_ns) q.done_ns[0] = globaltimer_ns();
+                const int2 e = q.queue[pos];
+                g = e.x;
+                local = e.y;
+                if (!wait_zero(q.counts + q.desc[g].count_base + local, q.status, q.timeout_ns, local, pos)) g = -1;
+                __threadfence();
+                fence_proxy_async_global();
+            }
+            s_g = g;
+            s_local = local;
+            s_pos = pos;
+        }
+        __syncthreads();
+        const int g = s_g;
+        if (g < 0) return;
+        const int local = s_local;
+        const BatchDesc& d = q.desc[g];
+        const int L1 = d.L1, L0 = d.L0;
+        const int ix = local % L1;
+        const int rest = local / L1;
+        const int iy = rest % L0;
+        const int b = rest / L0;
+        Args<T> B = A;
+        B.src = (const T*)d.buf[b & 1];
+        B.dst = (T*)d.buf[(b + 1) & 1];
+        B.g = d.g;
+        B.H = d.H;
+        B.Wt = d.Wt;
+        B.vec_ok = d.vec_ok != 0;
+        const int64_t x0 = (int64_t)ix * d.Wt, y0 = (int64_t)iy * d.H;
+        const int64_t olo = x0 + (int64_t)w * Wo;
+        int64_t ohi = olo + Wo;
+        if (ohi > x0 + d.Wt) ohi = x0 + d.Wt;
+        if (ohi > d.g.e[1]) ohi = d.g.e[1];
+        if (ohi < olo) ohi = olo;
+        const int depth = b < d.Pmain ? K : 1;
+        if constexpr (TMA) {
+            const CUtensorMap* map = &d.map[b & 1];
+            if (depth == K) {
+                warp_tile_any<T, EXACT, K, true, true>(B, map, r.ring, r.full, r.empty, nwarps, y0, olo, ohi, x0 - Kp,
+                                                       fill_base);
+                fill_base += (uint32_t)((d.H + 2 * K + kRingRows - 1) / kRingRows);
+            } else {
+                warp_tile_any<T, EXACT, 1, true, true>(B, map, r.ring, r.full, r.empty, nwarps, y0, olo, ohi, x0 - Kp,
+                                                       fill_base);
+                fill_base += (uint32_t)((d.H + 2 + kRingRows - 1) / kRingRows);
+            }
+        } else if (olo < ohi) {
+            (void)fill_base;
+            if (depth == K)
+                warp_tile_any<T, EXACT, K, true, false>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi, 0, 0);
+            else
+                warp_tile_any<T, EXACT, 1, true, false>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi, 0, 0);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (b + 1 < d.Ptotal) {
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int jy = iy + dy;
+                    if (jy < 0 || jy >= L0) continue;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int jx = ix + dx;
+                        if (jx < 0 || jx >= L1) continue;
+                        red_release_add_gpu(q.counts + d.count_base + ((b + 1) * L0 + jy) * L1 + jx, -1);
+                    }
+                }
+            }
+            if (atomicSub(q.remaining + g, 1) == 1 && q.done_ns) q.done_ns[1 + g] = globaltimer_ns();
+        }
+    }
+}
+
+// Copy the Dirichlet ring of every grid of the batch into its twin.
+template <class T>
+__global__ void batch_ring_kernel(BatchDev q) {
+    const BatchDesc& d = q.desc[blockIdx.x];
+    if (d.g.periodic) return;
+    const T* src = (const T*)d.buf[0];
+    T* dst = (T*)d.buf[1];
+    const int64_t ey = d.g.e[0], ex = d.g.e[1], P = d.g.s[0];
+    for (int64_t x = threadIdx.x; x < ex; x += blockDim.x) {
+        dst[x] = src[x];
+        dst[(ey - 1) * P + x] = src[(ey - 1) * P + x];
+    }
+    for (int64_t y = threadIdx.x; y < ey; y += blockDim.x) {
+        dst[y * P] = src[y * P];
+        dst[y * P + ex - 1] = src[y * P + ex - 1];
+    }
+}
+
+// Grids whose block count is odd end in their twin: copy it back.
+template <class T>
+__global__ void batch_copy_kernel(BatchDev q) {
+    const BatchDesc& d = q.desc[blockIdx.y];
+    if (!d.final_copy) return;
+    const T* src = (const T*)d.buf[1];
+    T* dst = (T*)d.buf[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.span; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+template <class T>
+size_t batch_smem(const BatchDev& q) {
+    return 128 + (size_t)kRingSlots * q.slot_elems * sizeof(T) + 2 * kRingSlots * sizeof(uint64_t);
+}
+
+template <class T, bool EXACT, int K>
+cudaError_t batch_launch_k(const double* coeffs, const BatchDev& q, int nwarps, int nctas, cudaStream_t s) {
+    const size_t sm = batch_smem<T>(q);
+    if (q.all_tma) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, EXACT, K, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        batch_kernel<T, EXACT, K, true><<<nctas, 32 * nwarps, sm, s>>>(q, coeffs_as<T>(coeffs));
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, EXACT, K, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        batch_kernel<T, EXACT, K, false><<<nctas, 32 * nwarps, sm, s>>>(q, coeffs_as<T>(coeffs));
+    }
+    return cudaGetLastError();
+}
+
+template <class T, bool EXACT, int K>
+int batch_occ_k(const BatchDev& q, int nwarps) {
+    const size_t sm = batch_smem<T>(q);
+    int n = 0;
+    if (q.all_tma) {
+        if (cudaFuncSetAttribute(batch_kernel<T, EXACT, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess)
+            return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<T, EXACT, K, true>, 32 * nwarps, sm) !=
+            cudaSuccess)
+            return 1;
+    } else {
+        if (cudaFuncSetAttribute(batch_kernel<T, EXACT, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm) != cudaSuccess)
+            return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<T, EXACT, K, false>, 32 * nwarps, sm) !=
+            cudaSuccess)
+            return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 }  // namespace
+
+int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
 
 int depths(int dtype, int* out, int cap) {
     static const int f32[] = {1, 2, 3, 4, 6, 8};
@@ -539,6 +715,22 @@ int depths(int dtype, int* out, int cap) {
     const int n = dtype == kF32 ? 6 : 4;
     for (int i = 0; i < n && i < cap; ++i) out[i] = src[i];
     return n;
+}
+
+// Resident CTAs of the single-level kernel on the whole GPU (0 if no device).
+int resident_slots(const LaunchCtx& L, int depth, int nwarps, int64_t Wt) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    TileGeo t{};
+    t.depth = depth;
+    t.nwarps = nwarps;
+    t.ext[1] = Wt;
+    const int per = ctas_per_sm(L, t);
+    return per > 0 ? per * sms : 0;
 }
 
 bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t) {
@@ -550,22 +742,135 @@ bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t) {
     if (!ok) return false;
     const int E = L.dtype == kF32 ? 4 : 2;
     const int Wo = wo_for(depth, E);
-    int64_t H = req && req[0] > 0 ? req[0] : 128;
-    int64_t Wreq = req && req[1] > 0 ? req[1] : 2 * Wo;
+    int64_t Wreq = req && req[1] > 0 ? req[1] : Wo;
     int nw = (int)((Wreq + Wo / 2) / Wo);
     if (nw < 1) nw = 1;
     if (nw > kMaxWarps) nw = kMaxWarps;
+    const int64_t Wt = (int64_t)nw * Wo;
+    const int64_t ey = L.geo.e[0];
+    const int64_t Lx = (L.geo.e[1] + Wt - 1) / Wt;
+    int64_t H = req && req[0] > 0 ? req[0] : 0;
+    if (H == 0) {
+        // Default height: the tallest tiles (least halo work) whose count
+        // fills whole waves of resident CTAs, so no partial last wave idles
+        // most of the GPU.  Without a device the height is a fixed 128.
+        H = 128;
+        const int slots = resident_slots(L, depth, nw, Wt);
+        const int64_t hmin = std::max<int64_t>(16, 4 * depth), hmax = 512;
+        if (slots > 0) {
+            for (int64_t m = 1; m <= 64; ++m) {
+                const int64_t Ly = m * slots / Lx;
+                if (Ly < 1) continue;
+                const int64_t h = (ey + Ly - 1) / Ly;
+                if (h <= hmax) {
+                    H = std::max(h, std::min(hmin, ey));
+                    break;
+                }
+            }
+        }
+    }
     if (H < depth) H = depth;  // the halo must stay within the neighbouring tile
     t->family = kFamStream2D;
     t->depth = depth;
     t->nwarps = nw;
     t->ext[0] = H;
-    t->ext[1] = (int64_t)nw * Wo;
+    t->ext[1] = Wt;
     t->ext[2] = 1;
-    t->count[0] = (L.geo.e[0] + H - 1) / H;
-    t->count[1] = (L.geo.e[1] + t->ext[1] - 1) / t->ext[1];
+    t->count[0] = (ey + H - 1) / H;
+    t->count[1] = Lx;
     t->count[2] = 1;
     return true;
+}
+
+
+bool batch_tiles(const LaunchCtx& L, int depth, int nwarps, int64_t H, TileGeo* t) {
+    if (L.geo.dims != 2 || L.geo.periodic) return false;
+    int ds[16];
+    const int nd = depths(L.dtype, ds, 16);
+    bool ok = false;
+    for (int i = 0; i < nd; ++i) ok = ok || ds[i] == depth;
+    if (!ok || nwarps < 1 || nwarps > kMaxWarps) return false;
+    const int E = L.dtype == kF32 ? 4 : 2;
+    const int64_t Wt = (int64_t)nwarps * wo_for(depth, E);
+    if (H < depth) H = depth;
+    t->family = kFamStream2D;
+    t->depth = depth;
+    t->nwarps = nwarps;
+    t->ext[0] = H;
+    t->ext[1] = Wt;
+    t->ext[2] = 1;
+    t->count[0] = (L.geo.e[0] + H - 1) / H;
+    t->count[1] = (L.geo.e[1] + Wt - 1) / Wt;
+    t->count[2] = 1;
+    return true;
+}
+
+bool batch_desc_tma(const LaunchCtx& L, const TileGeo& t, BatchDesc* d, BatchDev* ring) {
+    const void* bufs[2] = {d->buf[0], d->buf[1]};
+    CUtensorMap maps[2];
+    bool ok;
+    if (L.dtype == kF32) {
+        Args<float> A{};
+        A.vec_ok = d->vec_ok != 0;
+        ok = tma_setup<float>(L, t, &A, bufs, maps);
+        if (ok) {
+            ring->nbox = A.nbox; ring->BW = A.BW; ring->box_elems = A.box_elems; ring->slot_elems = A.slot_elems;
+        }
+    } else {
+        Args<double> A{};
+        A.vec_ok = d->vec_ok != 0;
+        ok = tma_setup<double>(L, t, &A, bufs, maps);
+        if (ok) {
+            ring->nbox = A.nbox; ring->BW = A.BW; ring->box_elems = A.box_elems; ring->slot_elems = A.slot_elems;
+        }
+    }
+    if (ok) {
+        d->map[0] = maps[0];
+        d->map[1] = maps[1];
+    }
+    d->tma_ok = ok ? 1 : 0;
+    return ok;
+}
+
+#define PCOT_BATCH_DISPATCH(FN, ...)                                                      \
+    switch (depth) {                                                                      \
+        case 1: if (dtype == kF32) return FN<float, false, 1>(__VA_ARGS__);               \
+                if (dtype == kF64) return FN<double, false, 1>(__VA_ARGS__);              \
+                return FN<double, true, 1>(__VA_ARGS__);                                  \
+        case 2: if (dtype == kF32) return FN<float, false, 2>(__VA_ARGS__);               \
+                if (dtype == kF64) return FN<double, false, 2>(__VA_ARGS__);              \
+                return FN<double, true, 2>(__VA_ARGS__);                                  \
+        case 4: if (dtype == kF32) return FN<float, false, 4>(__VA_ARGS__);               \
+                if (dtype == kF64) return FN<double, false, 4>(__VA_ARGS__);              \
+                return FN<double, true, 4>(__VA_ARGS__);                                  \
+        case 8: if (dtype == kF32) return FN<float, false, 8>(__VA_ARGS__);               \
+                break;                                                                    \
+    }
+
+cudaError_t batch_launch(int dtype, int depth, int nwarps, const double* coeffs, const BatchDev& q, int nctas,
+                         cudaStream_t s) {
+    PCOT_BATCH_DISPATCH(batch_launch_k, coeffs, q, nwarps, nctas, s)
+    return cudaErrorInvalidValue;
+}
+
+int batch_ctas_per_sm(int dtype, int depth, int nwarps, const BatchDev& q) {
+    PCOT_BATCH_DISPATCH(batch_occ_k, q, nwarps)
+    return 1;
+}
+
+#undef PCOT_BATCH_DISPATCH
+
+cudaError_t batch_final_copy(int dtype, const BatchDev& q, cudaStream_t s) {
+    dim3 grd(64, (unsigned)q.nb);
+    if (dtype == kF32) batch_copy_kernel<float><<<grd, 256, 0, s>>>(q);
+    else batch_copy_kernel<double><<<grd, 256, 0, s>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_ring_copy(int dtype, const BatchDev& q, cudaStream_t s) {
+    if (dtype == kF32) batch_ring_kernel<float><<<q.nb, 256, 0, s>>>(q);
+    else batch_ring_kernel<double><<<q.nb, 256, 0, s>>>(q);
+    return cudaGetLastError();
 }
 
 #define PCOT_F64_DEPTHS(X) X(1) X(2) X(3) X(4)

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) sweep3d_kernel(const T* __restrict__ src,
 // load at each end of the span.  Used when rows are 16-byte aligned and, for
 // periodic grids, the contiguous extent is a multiple of the warp span.
 template <class T, bool EXACT, int R>
-__global__ void __launch_bounds__(256) sweep2d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
+__global__ void __launch_bounds__(256, 4) sweep2d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
                                                           Coeffs<T> c) {
     constexpr int E = Vec<T>::E;
     using V = typename Vec<T>::V;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) sweep2d_vec_kernel(const T* __restrict__ 
 }
 
 template <class T, bool EXACT, int R>
-__global__ void __launch_bounds__(256) sweep3d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
+__global__ void __launch_bounds__(256, 4) sweep3d_vec_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
                                                           Coeffs<T> c) {
     constexpr int E = Vec<T>::E;
     using V = typename Vec<T>::V;
@@ -295,13 +295,13 @@ cudaError_t sweep_t(const LaunchCtx& L, const void* src, void* dst) {
         dim3 blk(256), grd((unsigned)((g.n[0] + 255) / 256));
         sweep1d_kernel<T, EXACT><<<grd, blk, 0, L.stream>>>(s, d, g, c);
     } else if (g.dims == 2 && sweep_vec_ok<T>(g, src, dst)) {
-        constexpr int R = 8;
+        constexpr int R = 4;
         constexpr int E = Vec<T>::E;
         dim3 grd((unsigned)((g.e[1] + 32 * E - 1) / (32 * E)), (unsigned)((g.n[0] + 8 * R - 1) / (8 * R)));
         if (grd.y > 65535) return cudaErrorInvalidConfiguration;
         sweep2d_vec_kernel<T, EXACT, R><<<grd, 256, 0, L.stream>>>(s, d, g, c);
     } else if (g.dims == 3 && sweep_vec_ok<T>(g, src, dst)) {
-        constexpr int R = 4;
+        constexpr int R = 2;
         constexpr int E = Vec<T>::E;
         dim3 grd((unsigned)((g.e[2] + 32 * E - 1) / (32 * E)), (unsigned)((g.n[1] + 7) / 8),
                  (unsigned)((g.n[0] + R - 1) / R));

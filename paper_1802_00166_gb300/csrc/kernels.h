@@ -68,6 +68,18 @@ int cot_ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
 // Dynamic shared memory of one CTA for this geometry.
 size_t tile_smem_bytes(const LaunchCtx& L, const TileGeo& t);
 
+// ---- k_mlp.cu ----
+namespace mlp {
+int param_count();
+size_t scratch_bytes(int batch);
+cudaError_t forward(const float* P, const float* X, int B, float* Y, cudaStream_t s);
+cudaError_t grad(const float* P, const float* X, const float* Tg, int B, float* G, float* loss, void* scratch,
+                 cudaStream_t s);
+cudaError_t adam(float* P, const float* G, float* M, float* V, int n, int step, float lr, float b1, float b2,
+                 float eps, cudaStream_t s);
+cudaError_t argmin(const float* Y, int n, int stride, int col, int* out, cudaStream_t s);
+}  // namespace mlp
+
 // ---- k_misc ----
 cudaError_t launch_wait_timeout_probe(int32_t* counter, DevStatus* st, uint64_t timeout_ns,
                                       cudaStream_t s);

@@ -1,6 +1,8 @@
 // Internal interface between the kernel families and the dispatcher.
 #pragma once
 
+#include <cuda.h>
+
 #include "kernels.h"
 
 namespace pcot {
@@ -62,6 +64,38 @@ __device__ __forceinline__ int pop_and_wait(const CotDev& q) {
     return tile;
 }
 
+// ---- batched persistent launch (many 2-D grids, one kernel) -------------
+// Per-grid descriptor, device resident.  Block b of grid g reads buf[b%2] and
+// writes buf[(b+1)%2]; blocks < Pmain advance `depth` steps, later blocks one.
+struct alignas(128) BatchDesc {
+    CUtensorMap map[2];   // TMA maps of buf[0] and buf[1] (valid when tma_ok)
+    void* buf[2];         // buf[0]: the caller's grid, buf[1]: its twin
+    DevGeo g;
+    int64_t H, Wt;        // tile height and width
+    int32_t L0, L1;       // tiles along axis 0 and axis 1
+    int32_t Pmain, Ptotal;
+    int32_t count_base;   // first dependency counter of this grid
+    int32_t ntiles;
+    int32_t vec_ok, tma_ok;
+    int32_t final_copy;   // odd block count: copy buf[1] back into buf[0] at the end
+    int64_t span;         // elements spanned by the grid's layout
+};
+
+struct BatchDev {
+    const BatchDesc* desc;
+    const int2* queue;    // (grid, local tile id) in execution order
+    int32_t* counts;
+    int32_t* remaining;   // tiles left per grid
+    int32_t* head;
+    int64_t ntiles;
+    uint64_t* done_ns;    // [0] start, [1+g] completion of grid g (may be NULL)
+    DevStatus* status;
+    uint64_t timeout_ns;
+    int nb;
+    int nbox, BW, box_elems, slot_elems;  // TMA ring geometry (common)
+    int all_tma;                          // every grid uses the TMA ring
+};
+
 // Family entry points (one per kernel family).
 namespace stream2d {
 bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t);
@@ -69,6 +103,14 @@ int depths(int dtype, int* out, int cap);
 cudaError_t slt(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst, DevStatus* st);
 cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas);
 int ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
+// Batched launch: common depth and warps, per-grid height.
+bool batch_tiles(const LaunchCtx& L, int depth, int nwarps, int64_t H, TileGeo* t);
+bool batch_desc_tma(const LaunchCtx& L, const TileGeo& t, BatchDesc* d, BatchDev* ring);
+cudaError_t batch_launch(int dtype, int depth, int nwarps, const double* coeffs, const BatchDev& q, int nctas,
+                         cudaStream_t s);
+int batch_ctas_per_sm(int dtype, int depth, int nwarps, const BatchDev& q);
+cudaError_t batch_ring_copy(int dtype, const BatchDev& q, cudaStream_t s);
+cudaError_t batch_final_copy(int dtype, const BatchDev& q, cudaStream_t s);
 }  // namespace stream2d
 
 namespace stream3d {

@@ -1,0 +1,123 @@
+"""The picker's MLP kernels against the FP64 oracle MLP, the autotuner, and
+the picker's consistency with its own forward pass."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+import seeded_inputs as si
+
+torch = pytest.importorskip("torch")
+pcot = pytest.importorskip("paper_1802_00166_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00166_gb300 import build
+    build.build()
+
+
+def _params(seed):
+    p = omlp.init_params(si.uniform01(seed, omlp.n_params()))
+    return p + 0.05 * (si.uniform01(seed + 1, p.size) - 0.5)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("B", [1, 7, 32, 100, 257])
+def test_forward_matches_oracle(B):
+    p = _params(3)
+    x = 2 * si.uniform01(4, B * 12).reshape(B, 12) - 1
+    y = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    pcot.pcot_mlp_forward(_dev(p), _dev(x), B, y)
+    ref, _ = omlp.forward(p.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("B", [5, 64, 130])
+def test_gradient_matches_oracle(B):
+    p = _params(7).astype(np.float32).astype(np.float64)
+    x = (2 * si.uniform01(8, B * 12).reshape(B, 12) - 1).astype(np.float32).astype(np.float64)
+    t = si.uniform01(9, B * 2).reshape(B, 2).astype(np.float32).astype(np.float64)
+    g = torch.empty(pcot.pcot_mlp_param_count(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sb = pcot.pcot_mlp_scratch_bytes(B)
+    scratch = torch.empty(sb, dtype=torch.uint8, device="cuda")
+    pcot.pcot_mlp_grad(_dev(p), _dev(x), _dev(t), B, g, loss, scratch, sb)
+    ref = omlp.backward(p, x, t)
+    got = g.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * max(1e-3, np.max(np.abs(ref)))
+    assert abs(float(loss.item()) - omlp.loss(p, x, t)) <= 1e-4 * max(1.0, omlp.loss(p, x, t))
+    # deterministic: the same call twice gives bitwise identical gradients
+    g2 = torch.empty_like(g)
+    pcot.pcot_mlp_grad(_dev(p), _dev(x), _dev(t), B, g2, None, scratch, sb)
+    assert torch.equal(g, g2)
+
+
+def test_adam_matches_oracle():
+    n = 1000
+    p = si.uniform01(11, n) - 0.5
+    m = 0.1 * (si.uniform01(12, n) - 0.5)
+    v = 0.01 * si.uniform01(13, n)
+    g = si.uniform01(14, n) - 0.5
+    P, M, V = _dev(p), _dev(m), _dev(v)
+    pcot.pcot_mlp_adam(P, _dev(g), M, V, n, 7, lr=3e-3)
+    rp, rm, rv = omlp.adam_step(p, g, m, v, 7, lr=3e-3)
+    assert np.max(np.abs(P.cpu().numpy() - rp)) <= 1e-6
+    assert np.max(np.abs(M.cpu().numpy() - rm)) <= 1e-7
+    assert np.max(np.abs(V.cpu().numpy() - rv)) <= 1e-7
+
+
+def test_argmin():
+    y = np.stack([si.uniform01(20, 300), si.uniform01(21, 300)], axis=1)
+    y[123, 0] = -5.0
+    y[200, 0] = -5.0   # tie: the lower index wins
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pcot.pcot_mlp_argmin(_dev(y), 300, 2, 0, out)
+    assert int(out.item()) == 123
+    pcot.pcot_mlp_argmin(_dev(y), 300, 2, 1, out)
+    assert int(out.item()) == int(np.argmin(y[:, 1]))
+
+
+def test_training_with_kernels_fits_a_function():
+    from paper_1802_00166_gb300 import tuner
+    x = 2 * si.uniform01(30, 2048 * 12).reshape(2048, 12) - 1
+    y = np.stack([x[:, 0] * 2 + x[:, 1] ** 2, np.sin(3 * x[:, 2])], axis=1)
+    picker, hist = tuner.train(x, y, steps=1500, batch=128, lr=3e-3, log_every=1500)
+    pred = picker.predict((x - picker.feat_mean) / picker.feat_std) * picker.targ_std + picker.targ_mean
+    assert np.mean((pred - y) ** 2) < 0.1 * np.mean((y - y.mean(0)) ** 2)
+
+
+def test_autotune_and_pick_consistency():
+    from paper_1802_00166_gb300 import tuner
+    prob = dict(dims=2, sizes=(700, 900), T=24, periodic=False)
+    cands, ms, feats = tuner.tune_problem(prob, reps=1)
+    assert len(ms) == len(cands) and all(t > 0 for t in ms)
+    picker = tuner.Picker(tuner.init_params(3), feats.mean(0), feats.std(0) + 1e-3, np.zeros(2), np.ones(2))
+    h = pcot.pcot_create(2, 1, tuner.HEAT2D, pcot.PCOT_DIRICHLET)
+    i = picker.pick(h, prob["sizes"], prob["T"], pcot.PCOT_F32, cands)
+    pcot.pcot_destroy(h)
+    pred = picker.predict((feats - picker.feat_mean) / picker.feat_std)
+    assert i == int(np.argmin(pred[:, 0]))
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                    "paper_1802_00166_gb300", "data", "picker.npz")),
+                    reason="no trained picker weights committed")
+def test_trained_picker_regret_on_heldout_sample():
+    """The committed model picks within 10% (time-weighted) of the exhaustive
+    tuner's best on a held-out sample, and beats the fixed default tile."""
+    from paper_1802_00166_gb300 import tuner
+    picker = tuner.Picker.load()
+    held = tuner.problem_set(5, 32, 32)
+    sample = held[0:32:8] + held[32:64:8]
+    summary, rows = tuner.evaluate(picker, sample)
+    assert summary["regret_time_weighted"] <= 0.10, summary
+    assert summary["regret_mean"] <= summary["default_regret_mean"], summary
