@@ -33,8 +33,8 @@ HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
 METRIC = "GUpdates/s & DRAM bytes/update vs plain sweep; % HBM roofline at stated error"
 UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
-BEST = {"schedule": "slt", "tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
-BEST_COT = {"schedule": "cot", "tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
+BEST = {"schedule": "slt", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
+BEST_COT = {"schedule": "cot", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 

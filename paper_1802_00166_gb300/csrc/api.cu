@@ -542,11 +542,11 @@ pcot_status build_batch_plan(pcot_handle h, int nb, const int64_t* sizes, const 
         if (!stream2d::batch_tiles(B->ctx[g], d, B->nwarps, H, &B->tg[g])) return PCOT_ERR_UNSUPPORTED;
         int64_t Pm = T[g] / d, tail = T[g] - Pm * d;
         if ((Pm + tail) % 2 == 1) {
-            if (Pm > 0) {
-                Pm -= 1;
+            if (Pm > 0 && d % 2 == 0) {
+                Pm -= 1;  // one block of depth d becomes d single steps: the count turns even
                 tail += d;
             } else {
-                B->final_copy[g] = 1;  // odd T below the depth: the result is copied back at the end
+                B->final_copy[g] = 1;  // the result ends in the twin and is copied back at the end
                 B->any_final_copy = true;
             }
         }

@@ -562,7 +562,16 @@ __global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeff
                 const int2 e = q.queue[pos];
                 g = e.x;
                 local = e.y;
-                if (!wait_zero(q.counts + q.desc[g].count_base + local, q.status, q.timeout_ns, local, pos)) g = -1;
+                if (g < 0 || g >= q.nb || local < 0 || local >= q.desc[g].ntiles) {
+                    if (atomicCAS(&q.status->code, 0, kStatusBounds) == 0) {
+                        q.status->info[0] = pos;
+                        q.status->info[1] = g;
+                    }
+                    atomicExch(&q.status->abort, 1);
+                    g = -1;
+                } else if (!wait_zero(q.counts + q.desc[g].count_base + local, q.status, q.timeout_ns, local, pos)) {
+                    g = -1;
+                }
                 __threadfence();
                 fence_proxy_async_global();
             }
@@ -596,6 +605,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeff
         const int depth = b < d.Pmain ? K : 1;
         if constexpr (TMA) {
             const CUtensorMap* map = &d.map[b & 1];
+            if (threadIdx.x == 0) fence_tensormap_acquire(map);
             if (depth == K) {
                 warp_tile_any<T, EXACT, K, true, true>(B, map, r.ring, r.full, r.empty, nwarps, y0, olo, ohi, x0 - Kp,
                                                        fill_base);
@@ -622,7 +632,12 @@ __global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeff
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int jx = ix + dx;
                         if (jx < 0 || jx >= L1) continue;
-                        red_release_add_gpu(q.counts + d.count_base + ((b + 1) * L0 + jy) * L1 + jx, -1);
+                        const int succ = ((b + 1) * L0 + jy) * L1 + jx;
+                        if (succ >= d.ntiles) {
+                            atomicCAS(&q.status->code, 0, kStatusBounds);
+                            continue;
+                        }
+                        red_release_add_gpu(q.counts + d.count_base + succ, -1);
                     }
                 }
             }

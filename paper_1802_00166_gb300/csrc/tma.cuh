@@ -76,6 +76,14 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Before the first use of a tensor map that lives in global memory and was
+// written through the generic proxy (a copy from the host): makes the
+// tensormap proxy observe that content rather than a descriptor cached for
+// the same address by an earlier launch.
+__device__ __forceinline__ void fence_tensormap_acquire(const void* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)map) : "memory");
+}
+
 // Host: encode a 2-D row-major tensor map (innermost dimension first).
 // Returns false if the driver entry point is unavailable or encoding fails.
 bool encode_tmap_2d(CUtensorMap* map, const void* base, int elem_bytes, uint64_t width, uint64_t height,
