@@ -58,13 +58,17 @@ struct Args {
 
 // One warp's trapezoid.  x_cta: first column of the CTA's span (TMA ring
 // origin); fill_base: fills of the ring consumed before this tile (COT).
-template <class T, bool EXACT, int K, bool CG, bool TMA, bool CHECK>
+// KPS: columns of the warp span left of the output (at least the halo of K
+// steps; a single-step tile inside a deeper tile geometry keeps that
+// geometry's span so it reads the same ring columns).
+template <class T, bool EXACT, int K, bool CG, bool TMA, bool CHECK, int KPS>
 __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* tmap, T* ring, uint64_t* full,
                                           uint64_t* empty, int nwarps, int64_t y0, int64_t olo, int64_t ohi,
                                           int64_t x_cta, uint32_t fill_base) {
     constexpr int E = Vec<T>::E;
     using V = typename Vec<T>::V;
-    constexpr int Kp = Shape<K, E>::Kp;
+    constexpr int Kp = KPS;
+    static_assert(KPS >= K && KPS % E == 0 && 2 * KPS < 32 * E, "warp span too small for the halo");
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const DevGeo& g = A.g;
@@ -137,7 +141,11 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     // ---- TMA path ----------------------------------------------------------
     const bool producer = TMA && warp == 0 && lane == 0;
     const int nfill = (nrows + kRingRows - 1) / kRingRows;
-    const int col_off = (int)(olo - Kp - x_cta) + lane * E;  // column inside the CTA span
+    int col_off = (int)(olo - Kp - x_cta) + lane * E;  // column inside the CTA span
+    if (TMA && (col_off < 0 || col_off + E > A.nbox * A.BW)) {
+        if (atomicCAS(&A.st->code, 0, kStatusBounds) == 0) A.st->info[3] = col_off;
+        col_off = 0;  // never read outside the ring
+    }
     const int box = TMA ? col_off / A.BW : 0;
     const int cc = TMA ? col_off - box * A.BW : 0;
     auto issue = [&](int f) {
@@ -257,23 +265,24 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
 }
 
 // Does any cell this warp computes need the Dirichlet pass-through?
-template <int K, int E>
+template <int K, int E, int KPS>
 __device__ __forceinline__ bool needs_check(const DevGeo& g, int64_t y0, int64_t H, int64_t olo) {
     if (g.periodic) return false;
-    constexpr int Kp = Shape<K, E>::Kp;
+    constexpr int Kp = KPS;
     const int64_t xa = olo - Kp, xb = olo - Kp + 32 * E - 1;
     const int64_t ya = y0 - K - 1, yb = y0 + H + K;
     return !(xa >= 1 && xb <= g.n[1] && ya >= 1 && yb <= g.n[0]);
 }
 
-template <class T, bool EXACT, int K, bool CG, bool TMA>
+template <class T, bool EXACT, int K, bool CG, bool TMA, int KPS = Shape<K, Vec<T>::E>::Kp>
 __device__ __forceinline__ void warp_tile_any(const Args<T>& A, const CUtensorMap* tmap, T* ring, uint64_t* full,
                                               uint64_t* empty, int nwarps, int64_t y0, int64_t olo, int64_t ohi,
                                               int64_t x_cta, uint32_t fill_base) {
-    if (needs_check<K, Vec<T>::E>(A.g, y0, A.H, olo))
-        warp_tile<T, EXACT, K, CG, TMA, true>(A, tmap, ring, full, empty, nwarps, y0, olo, ohi, x_cta, fill_base);
+    if (needs_check<K, Vec<T>::E, KPS>(A.g, y0, A.H, olo))
+        warp_tile<T, EXACT, K, CG, TMA, true, KPS>(A, tmap, ring, full, empty, nwarps, y0, olo, ohi, x_cta, fill_base);
     else
-        warp_tile<T, EXACT, K, CG, TMA, false>(A, tmap, ring, full, empty, nwarps, y0, olo, ohi, x_cta, fill_base);
+        warp_tile<T, EXACT, K, CG, TMA, false, KPS>(A, tmap, ring, full, empty, nwarps, y0, olo, ohi, x_cta,
+                                                    fill_base);
 }
 
 template <class T>
@@ -611,8 +620,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeff
                                                        fill_base);
                 fill_base += (uint32_t)((d.H + 2 * K + kRingRows - 1) / kRingRows);
             } else {
-                warp_tile_any<T, EXACT, 1, true, true>(B, map, r.ring, r.full, r.empty, nwarps, y0, olo, ohi, x0 - Kp,
-                                                       fill_base);
+                warp_tile_any<T, EXACT, 1, true, true, Kp>(B, map, r.ring, r.full, r.empty, nwarps, y0, olo, ohi,
+                                                           x0 - Kp, fill_base);
                 fill_base += (uint32_t)((d.H + 2 + kRingRows - 1) / kRingRows);
             }
         } else if (olo < ohi) {
@@ -620,7 +629,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeff
             if (depth == K)
                 warp_tile_any<T, EXACT, K, true, false>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi, 0, 0);
             else
-                warp_tile_any<T, EXACT, 1, true, false>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi, 0, 0);
+                warp_tile_any<T, EXACT, 1, true, false, Kp>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi,
+                                                            0, 0);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
