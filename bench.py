@@ -347,6 +347,34 @@ def compare_schedules(pcot, h, base, sizes, strides, stream):
     return out
 
 
+def run_profile_case(args):
+    """One configuration run `--case-runs` times without timing (the command
+    the committed ncu summaries were captured with)."""
+    import torch
+
+    import paper_1802_00166_gb300 as pcot
+    from paper_1802_00166_gb300 import build as pbuild
+    pbuild.build()
+    n, T = args.case_n, args.case_T
+    H, W = (int(v) for v in args.case_tile.split(","))
+    th = tuple(int(v) for v in args.case_theta.split(","))
+    h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+    pitch = ((n + 2 + 31) // 32) * 32
+    base = torch.rand((n + 2) * pitch, device="cuda")
+    sched = pcot.SCHEDULES[args.profile_case]
+    p = pcot.tile_params(tile=(H, W), time_depth=args.case_k, cot_threshold=th)
+    nb = pcot.pcot_workspace_bytes(h, (n, n), (pitch, 1), T, pcot.PCOT_F32, sched, p)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    for _ in range(args.case_runs):
+        pcot.pcot_run(h, base.data_ptr(), ws.data_ptr(), nb, (n, n), (pitch, 1), T, pcot.PCOT_F32, sched, p)
+    st = pcot.pcot_check(h)
+    pcot.pcot_destroy(h)
+    if st != pcot.PCOT_OK:
+        raise pcot.PcotError(st, "profile case")
+    print(f"ok {args.profile_case} n={n} T={T} k={args.case_k} tile={H},{W} theta={th}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +384,17 @@ def main():
     ap.add_argument("--schedule", default=None, choices=[None, "sweep", "slt", "cot"])
     ap.add_argument("--schedules", action="store_true", help="also time sweep / SLT / COT side by side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
+                    help="run one Heat-2D configuration (no timing) for a profiler")
+    ap.add_argument("--case-n", type=int, default=8192)
+    ap.add_argument("--case-T", type=int, default=64)
+    ap.add_argument("--case-k", type=int, default=8)
+    ap.add_argument("--case-tile", default="96,112")
+    ap.add_argument("--case-theta", default="2,256,256")
+    ap.add_argument("--case-runs", type=int, default=2)
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
