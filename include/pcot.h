@@ -321,6 +321,33 @@ pcot_status pcot_pick(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype
                       int ncand, const pcot_schedule *schedules, const pcot_tile_params *params,
                       void *scratch, int *best, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant of pcot_run (the paper has no counterpart; it
+ * serves callers that may not allocate device memory when they advance a
+ * grid: code running while a CUDA graph is captured, hosts that reserve all
+ * device memory up front, layers handed only a grid and a stream).
+ *
+ * Runs PCOT_SWEEP or PCOT_SLT exactly like pcot_run, but the grid's twin
+ * is a fixed array of PCOT_NOALLOC_MAX_BYTES bytes that the library
+ * reserves on every GPU that loads it, for the life of the process; the call
+ * allocates nothing (no cudaMalloc, no host heap).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Grids whose storage span
+ * exceeds PCOT_NOALLOC_MAX_BYTES return PCOT_ERR_OOM; PCOT_COT and
+ * PCOT_AUTO return PCOT_ERR_UNSUPPORTED.  All calls on one device share the
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.  The array keeps the
+ * previous call's contents; the call rewrites everything it reads (the ring
+ * is copied in first).  Tiles use plain loads (no TMA ring), so no device
+ * status block is needed; launch errors are returned, pcot_check is not
+ * required.
+ * ------------------------------------------------------------------------ */
+#define PCOT_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
+
+pcot_status pcot_run_noalloc(pcot_handle h, void *grid, const int64_t *sizes, const int64_t *strides,
+                             int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                             const pcot_tile_params *params, void *stream);
+
 /*
  * Number of kernels this handle has launched since it was created (sweep
  * steps, single-level blocks, persistent executors, ring copies, sums).

@@ -114,6 +114,8 @@ def _load():
         "pcot_mlp_argmin": (S, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]),
         "pcot_features": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
                               ctypes.POINTER(ctypes.c_float)]),
+        "pcot_run_noalloc": (S, [_VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
@@ -133,7 +135,7 @@ def exported_symbols():
             "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
             "pcot_batch_destroy", "pcot_run_batched", "pcot_autotune", "pcot_mlp_param_count",
             "pcot_mlp_scratch_bytes", "pcot_mlp_forward", "pcot_mlp_grad", "pcot_mlp_adam", "pcot_mlp_argmin",
-            "pcot_features", "pcot_pick"]
+            "pcot_features", "pcot_pick", "pcot_run_noalloc"]
 
 
 def status_string(s):
@@ -212,6 +214,16 @@ def pcot_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, sche
     s, st = _i64(sizes), _i64(strides)
     _chk(_load().pcot_run(h, _ptr(grid), _ptr(workspace), int(workspace_bytes), _p64(s), _p64(st), int(T),
                           int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_run")
+
+
+NOALLOC_MAX_BYTES = 32 * 1024 * 1024
+
+
+def pcot_run_noalloc(h, grid, sizes, strides, T, dtype, schedule, params=None, stream=None):
+    """pcot_run without a workspace: the library's fixed device array is the twin."""
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_run_noalloc(h, _ptr(grid), _p64(s), _p64(st), int(T), int(dtype), int(schedule),
+                                  _params(params), _stream(stream)), "pcot_run_noalloc")
 
 
 def pcot_run_host(h, host_grid, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,

@@ -960,3 +960,17 @@ pcot_status pcot_pick(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype
 }
 
 }  // extern "C"
+
+// Handle fields for the allocation-free entry point (api_noalloc.cu).
+namespace pcot {
+pcot_status handle_describe(pcot_handle h, int* dims, int* periodic, double* coeffs7) {
+    if (!h) return PCOT_ERR_INVALID_ARG;
+    *dims = h->dims;
+    *periodic = h->boundary == PCOT_PERIODIC ? 1 : 0;
+    for (int i = 0; i < 7; ++i) coeffs7[i] = h->coeffs[i];
+    return PCOT_OK;
+}
+void handle_count_launches(pcot_handle h, int64_t n) {
+    if (h) h->launches += n;
+}
+}  // namespace pcot
