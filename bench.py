@@ -103,22 +103,24 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _traffic_from_profile(kernel_tag):
-    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
-    valid only while the kernel sources hash to the value recorded there."""
-    path = os.path.join(ROOT, "profiles", "cot_heat2d_traffic.json")
+def _traffic_from_profile(kernel_tag, blocks_per_launch):
+    """DRAM bytes per launch of the timed kernel from the committed ncu
+    summary (bytes per time block x blocks per launch), or None when the
+    kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "heat2d_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
+        h = hashlib.sha256()
+        for fn in rec.get("sources", []):
+            with open(os.path.join(ROOT, fn), "rb") as f:
+                h.update(f.read())
     except Exception:
         return None
-    h = hashlib.sha256()
-    for fn in rec.get("sources", []):
-        with open(os.path.join(ROOT, fn), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != rec.get("sources_sha256") or rec.get("kernel") != kernel_tag:
+    per_block = rec.get("bytes_per_block", {}).get(kernel_tag)
+    if h.hexdigest() != rec.get("sources_sha256") or per_block is None:
         return None
-    return rec.get("bytes_per_launch_full")
+    return per_block * blocks_per_launch
 
 
 def _cpu_oracle_sample(seconds=12.0, threads=None):
@@ -285,7 +287,8 @@ def run_gpu(args):
     achieved = per_launch_bytes / launch_s / 1e9
     kernel_tag = f"{kname} f32 k={k} tile={q['tile_ext'][:2]}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic_from_profile(kernel_tag), "peak_kind": peak_kind,
+            "traffic": _traffic_from_profile(kernel_tag, blocks if sched == pcot.PCOT_COT else 1),
+            "peak_kind": peak_kind,
             "kernel": kernel_tag, "alg_bytes_per_launch": per_launch_bytes, "launches_per_step": launches_per_step,
             "model": "ceil(T/k) passes x (read + write of the 8192^2 fp32 grid)"}
 
