@@ -35,6 +35,7 @@ UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
 BEST = {"schedule": "slt", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
 BEST_COT = {"schedule": "cot", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
+BATCH = {"tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 8, 8)}
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 
@@ -313,12 +314,68 @@ def run_gpu(args):
                                 "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
     if args.schedules and rank == 0:
         line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
+    if args.batched and rank == 0:
+        del base, wsbuf, host
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(pcot, stream, args.steps)
     pcot.pcot_destroy(h)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(pcot, stream, steps):
+    """256 independent Heat-2D grids (sides log-uniform in [256, 2048], T in
+    [64, 1024], seeded) advanced by one persistent launch replayed from a CUDA
+    graph: throughput and per-grid completion latency (p50 / p99)."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    probs = si.batched_problem_set(seed=4, count=256)
+    h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+    grids, sizes, strides, Ts = [], [], [], []
+    updates = 0.0
+    for side, T, seed in probs:
+        shape = (side + 2, side + 2)
+        pitch = ((shape[1] + 31) // 32) * 32
+        base = torch.empty(pitch * shape[0], dtype=torch.float32, device="cuda")
+        torch.as_strided(base, shape, (pitch, 1)).copy_(
+            torch.from_numpy(si.uniform_grid((side, side), seed, dtype=np.float32)).cuda())
+        grids.append(base)
+        sizes += [side, side]
+        strides += [pitch, 1]
+        Ts.append(T)
+        updates += float(side) * side * T
+    params = [pcot.tile_params(tile=BATCH["tile"], time_depth=BATCH["time_depth"],
+                               cot_threshold=BATCH["cot_threshold"])] * len(probs)
+    nb = pcot.pcot_batch_workspace_bytes(h, sizes, strides, Ts, pcot.PCOT_F32, params)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    done = torch.zeros(len(probs) + 1, dtype=torch.int64, device="cuda")
+    b = pcot.pcot_batch_create(h, grids, sizes, strides, Ts, pcot.PCOT_F32, params, ws, nb, done, stream)
+    pcot.pcot_batch_launch(b, stream)
+    torch.cuda.synchronize()
+    reps = max(1, min(steps, 5))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        pcot.pcot_batch_launch(b, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = pcot.pcot_check(h, stream)
+    pcot.pcot_batch_destroy(b)
+    pcot.pcot_destroy(h)
+    if st != pcot.PCOT_OK:
+        raise pcot.PcotError(st, "batched")
+    ms = e0.elapsed_time(e1) / reps
+    d = done.cpu().numpy().astype(np.float64)
+    lat = (d[1:] - d[0]) / 1e6
+    return {"grids": len(probs), "updates": updates, "ms": ms, "GUpdates/s": updates / ms / 1e6,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "latency_ms_max": float(lat.max()), "params": BATCH, "launch": "one persistent kernel, CUDA graph"}
 
 
 def compare_schedules(pcot, h, base, sizes, strides, stream):
@@ -391,6 +448,7 @@ def main():
     ap.add_argument("--schedule", default=None, choices=[None, "sweep", "slt", "cot"])
     ap.add_argument("--schedules", action="store_true", help="also time sweep / SLT / COT side by side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true", help="also time the 256-grid batched persistent launch")
     ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
     ap.add_argument("--case-n", type=int, default=8192)

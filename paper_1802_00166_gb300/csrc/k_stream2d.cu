@@ -163,28 +163,6 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             for (int f = 0; f < kRingSlots - 1 && f < nfill; ++f) issue(f);
         }
     }
-    auto tma_row = [&](int i, T (&v)[E]) {
-        const int f = i / kRingRows, r = i - f * kRingRows;
-        const uint32_t gi = fill_base + (uint32_t)f;
-        const int slot = (int)(gi % kRingSlots);
-        if (r == 0) {
-            if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
-            mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
-        }
-        const T* p = ring + (size_t)slot * A.slot_elems + (size_t)box * A.box_elems + r * A.BW + cc;
-        const V q = *reinterpret_cast<const V*>(p);
-        const T* qq = reinterpret_cast<const T*>(&q);
-#pragma unroll
-        for (int j = 0; j < E; ++j) v[j] = qq[j];
-    };
-    auto tma_done = [&](int i) {
-        const int f = i / kRingRows, r = i - f * kRingRows;
-        if (r == kRingRows - 1 || i == nrows - 1) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[(fill_base + (uint32_t)f) % kRingSlots]);
-        }
-    };
-
     const bool warp_xint = __all_sync(kFull, xint[0] && xint[E - 1]);
 
     T R[K][3][E];
@@ -202,16 +180,42 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
         if (ybeg + 2 < yend) load_row(ybeg + 2, pf[2]);
     }
 
-    auto step = [&](auto Uc, int64_t yi) {
+    // 32-bit row bookkeeping relative to ybeg: step i reads input row ybeg+i
+    // and emits output row ro = y0 + i - 2K, stored for i in [ist_lo, ist_hi).
+    auto clamp32 = [](int64_t v) { return (int)(v < -(1LL << 30) ? -(1LL << 30) : v > (1LL << 30) ? (1LL << 30) : v); };
+    int ist_lo = 2 * K, ist_hi = 2 * K + (int)H;
+    if (per) {
+        ist_hi = min(ist_hi, clamp32(2 * K + ny - y0));
+    } else {
+        ist_lo = max(ist_lo, clamp32(2 * K + 1 - y0));
+        ist_hi = min(ist_hi, clamp32(2 * K + ny + 1 - y0));
+    }
+    // Rows of time level s+1 produced at step i are ybeg + i - s - 1; they are
+    // interior rows when i - s - 1 lies in [rlo, rhi].
+    const int rlo = clamp32(1 - ybeg), rhi = clamp32(ny - ybeg);
+    T* const dst_lane = A.dst + xl;
+    const int64_t out_row0 = y0 - 2 * K;
+    const T* lane_ring = TMA ? ring + (size_t)box * A.box_elems + cc : nullptr;
+
+    auto step = [&](auto Uc, int i) {
         constexpr int U = decltype(Uc)::value;
         constexpr int SA = U % 3, SB = (U + 1) % 3, SN = (U + 2) % 3;
-        const int i = (int)(yi - ybeg);
         if constexpr (TMA) {
-            tma_row(i, R[0][SN]);
+            const int f = i >> 2, r = i & (kRingRows - 1);
+            const uint32_t gi = fill_base + (uint32_t)f;
+            const int slot = (int)(gi & (kRingSlots - 1));
+            if (r == 0) {
+                if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
+                mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
+            }
+            const V q = *reinterpret_cast<const V*>(lane_ring + slot * A.slot_elems + r * A.BW);
+            const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) R[0][SN][j] = qq[j];
         } else {
 #pragma unroll
             for (int j = 0; j < E; ++j) R[0][SN][j] = pf[U][j];
-            if (yi + 3 < yend) load_row(yi + 3, pf[U]);
+            if (i + 3 < nrows) load_row(ybeg + i + 3, pf[U]);
         }
         T out[E];
 #pragma unroll
@@ -225,8 +229,8 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 out[j] = upd2<T, EXACT>(A.c, R[s][SB][j], R[s][SA][j], R[s][SN][j], W, Ea);
             }
             if constexpr (CHECK) {
-                const int64_t r = yi - s - 1;  // row of time level s+1 produced now
-                const bool rint = r >= 1 && r <= ny;
+                const int rr = i - s - 1;
+                const bool rint = rr >= rlo && rr <= rhi;
                 if (!(rint && warp_xint)) {
 #pragma unroll
                     for (int j = 0; j < E; ++j)
@@ -238,29 +242,57 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 for (int j = 0; j < E; ++j) R[s + 1][SN][j] = out[j];
             }
         }
-        if constexpr (TMA) tma_done(i);
-        const int64_t ro = yi - K;
-        const bool rok = ro >= y0 && ro < y0 + H && (per ? ro < ny : (ro >= 1 && ro <= ny));
-        if (rok) {
-            T* rowp = A.dst + ro * P;
+        if constexpr (TMA) {
+            const int r = i & (kRingRows - 1);
+            if (r == kRingRows - 1 || i == nrows - 1) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(fill_base + (uint32_t)(i >> 2)) & (kRingSlots - 1)]);
+            }
+        }
+        if (i >= ist_lo && i < ist_hi) {
+            T* rowp = dst_lane + (out_row0 + i) * P;
             if (svec) {
                 V q;
                 T* qq = reinterpret_cast<T*>(&q);
 #pragma unroll
                 for (int j = 0; j < E; ++j) qq[j] = out[j];
-                *reinterpret_cast<V*>(rowp + xl) = q;
+                *reinterpret_cast<V*>(rowp) = q;
             } else {
 #pragma unroll
                 for (int j = 0; j < E; ++j)
-                    if (st[j]) rowp[xl + j] = out[j];
+                    if (st[j]) rowp[j] = out[j];
             }
         }
     };
 
-    for (int64_t yi = ybeg; yi < yend; yi += 3) {
-        step(IC<0>{}, yi);
-        if (yi + 1 < yend) step(IC<1>{}, yi + 1);
-        if (yi + 2 < yend) step(IC<2>{}, yi + 2);
+    if constexpr (CHECK) {
+        // Boundary warps (a few per grid): one compact body and explicit
+        // rotation of the rings, to keep the instruction footprint small.
+        for (int i = 0; i < nrows; ++i) {
+            step(IC<0>{}, i);
+#pragma unroll
+            for (int s = 0; s < K; ++s)
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    R[s][0][j] = R[s][1][j];
+                    R[s][1][j] = R[s][2][j];
+                }
+            if constexpr (!TMA) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) {
+                    const T t0 = pf[0][j];
+                    pf[0][j] = pf[1][j];
+                    pf[1][j] = pf[2][j];
+                    pf[2][j] = t0;
+                }
+            }
+        }
+    } else {
+        for (int i = 0; i < nrows; i += 3) {
+            step(IC<0>{}, i);
+            if (i + 1 < nrows) step(IC<1>{}, i + 1);
+            if (i + 2 < nrows) step(IC<2>{}, i + 2);
+        }
     }
 }
 
