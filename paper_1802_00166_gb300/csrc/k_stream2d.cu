@@ -193,9 +193,8 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     // Rows of time level s+1 produced at step i are ybeg + i - s - 1; they are
     // interior rows when i - s - 1 lies in [rlo, rhi].
     const int rlo = clamp32(1 - ybeg), rhi = clamp32(ny - ybeg);
-    T* const dst_lane = A.dst + xl;
-    const int64_t out_row0 = y0 - 2 * K;
-    const T* lane_ring = TMA ? ring + (size_t)box * A.box_elems + cc : nullptr;
+    T* const dst_row0 = A.dst + xl + (y0 - 2 * K) * P;  // row of step 0 (only dereferenced in the store range)
+    const int lane_ring = TMA ? box * A.box_elems + cc : 0;
 
     auto step = [&](auto Uc, int i) {
         constexpr int U = decltype(Uc)::value;
@@ -208,7 +207,7 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
                 mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
             }
-            const V q = *reinterpret_cast<const V*>(lane_ring + slot * A.slot_elems + r * A.BW);
+            const V q = *reinterpret_cast<const V*>(ring + (lane_ring + slot * A.slot_elems + r * A.BW));
             const T* qq = reinterpret_cast<const T*>(&q);
 #pragma unroll
             for (int j = 0; j < E; ++j) R[0][SN][j] = qq[j];
@@ -250,7 +249,7 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             }
         }
         if (i >= ist_lo && i < ist_hi) {
-            T* rowp = dst_lane + (out_row0 + i) * P;
+            T* rowp = dst_row0 + (int64_t)i * P;
             if (svec) {
                 V q;
                 T* qq = reinterpret_cast<T*>(&q);
@@ -348,8 +347,12 @@ __device__ __forceinline__ void init_ring(const SmemRing<T>& r, int nwarps) {
     __syncthreads();
 }
 
+// Register budget of a K-stage tile (the stage rings hold 3*K*E values).
+template <int K>
+constexpr int kRegBudget = K >= 8 ? 184 : (K >= 6 ? 160 : 128);
+
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __launch_bounds__(32 * kMaxWarps) slt_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __maxnreg__(kRegBudget<K>) slt_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smraw[];
     constexpr int Wo = Shape<K, Vec<T>::E>::Wo;
     constexpr int Kp = Shape<K, Vec<T>::E>::Kp;
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(32 * kMaxWarps) slt_kernel(Args<T> A, const __
 }
 
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __launch_bounds__(32 * kMaxWarps) cot_kernel(Args<T> A, T* buf0, T* buf1, CotDev q,
+__global__ void __maxnreg__(kRegBudget<K>) cot_kernel(Args<T> A, T* buf0, T* buf1, CotDev q,
                                                              const __grid_constant__ CUtensorMap map0,
                                                              const __grid_constant__ CUtensorMap map1) {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -575,7 +578,7 @@ int occ_k(const LaunchCtx& L, const TileGeo& t) {
 
 // Persistent kernel over the merged tile queue of a batch of grids.
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __launch_bounds__(32 * kMaxWarps) batch_kernel(BatchDev q, Coeffs<T> c) {
+__global__ void __maxnreg__(kRegBudget<K>) batch_kernel(BatchDev q, Coeffs<T> c) {
     extern __shared__ __align__(128) unsigned char smraw[];
     constexpr int E = Vec<T>::E;
     constexpr int Wo = Shape<K, E>::Wo;
