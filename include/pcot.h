@@ -216,8 +216,8 @@ pcot_status pcot_grid_sum(pcot_handle h, const void *grid, const int64_t *sizes,
  *  sizes     nb*2 interior sizes (row-major per grid)
  *  strides   nb*2 element strides, or NULL for contiguous grids
  *  T         nb step counts (>= 0)
- *  params    nb tile parameter sets or NULL; time_depth (1, 2, 4 or 8 for
- *            PCOT_F32; 1, 2 or 4 otherwise) and tile[1] (warps per tile via
+ *  params    nb tile parameter sets or NULL; time_depth (1, 2, 4, 6 or 8
+ *            for PCOT_F32; 1, 2 or 4 otherwise) and tile[1] (warps per tile via
  *            the tile width) are taken from params[0] for all grids; tile[0]
  *            and cot_threshold per grid
  *  workspace device scratch of pcot_batch_workspace_bytes bytes (queue,

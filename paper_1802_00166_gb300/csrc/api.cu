@@ -521,7 +521,7 @@ pcot_status build_batch_plan(pcot_handle h, int nb, const int64_t* sizes, const 
     const int kdef = dtype == PCOT_F32 ? 8 : 2;
     B->depth = params && params[0].time_depth > 0 ? params[0].time_depth : kdef;
     const int d = B->depth;
-    if (!(d == 1 || d == 2 || d == 4 || (d == 8 && dtype == PCOT_F32))) return PCOT_ERR_UNSUPPORTED;
+    if (!(d == 1 || d == 2 || d == 4 || ((d == 6 || d == 8) && dtype == PCOT_F32))) return PCOT_ERR_UNSUPPORTED;
     const int E = dtype == PCOT_F32 ? 4 : 2;
     const int Kp = ((d + E - 1) / E) * E;
     const int Wo = 32 * E - 2 * Kp;

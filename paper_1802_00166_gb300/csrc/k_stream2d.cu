@@ -903,6 +903,8 @@ bool batch_desc_tma(const LaunchCtx& L, const TileGeo& t, BatchDesc* d, BatchDev
         case 4: if (dtype == kF32) return FN<float, false, 4>(__VA_ARGS__);               \
                 if (dtype == kF64) return FN<double, false, 4>(__VA_ARGS__);              \
                 return FN<double, true, 4>(__VA_ARGS__);                                  \
+        case 6: if (dtype == kF32) return FN<float, false, 6>(__VA_ARGS__);               \
+                break;                                                                    \
         case 8: if (dtype == kF32) return FN<float, false, 8>(__VA_ARGS__);               \
                 break;                                                                    \
     }
