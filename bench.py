@@ -1,10 +1,12 @@
 """Benchmark: Heat-2D 5-point Jacobi, 8192 x 8192 interior, T = 512 steps.
 
 One step = one call of the library's run entry point advancing the whole grid
-by T = 512 time steps in FP32 under the fastest tiled schedule found by the
-autotuner (BEST below): trapezoid tiles of depth k streamed through registers,
-fed by TMA; with --schedules the plain sweep and the recursive
-(cache-oblivious) persistent schedule are timed beside it.  Inputs are
+by T = 512 time steps in FP32 under the fastest schedule found by the
+autotuner (BEST below): the recursive-order persistent executor over the
+skewed (time block, tile) lattice, whose leaves are trapezoid tiles of depth k
+streamed through registers and fed by TMA.  With --schedules the plain sweep,
+the single-level schedule and a fine-grained recursive order (L2-sized leaves)
+are timed beside it.  Inputs are
 seeded synthetic U[0,1) values with a zero Dirichlet ring (resident in HBM
 before timing; the two 256 MiB buffers exceed the 129 MB L2, so no flush is
 needed between steps).
@@ -33,9 +35,9 @@ HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
 METRIC = "GUpdates/s & DRAM bytes/update vs plain sweep; % HBM roofline at stated error"
 UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
-BEST = {"schedule": "slt", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 64, 64)}
-BEST_COT = {"schedule": "cot", "tile": (96, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
-BATCH = {"tile": (64, 112), "time_depth": 8, "cot_threshold": (2, 8, 8)}
+BEST = {"schedule": "cot", "tile": (96, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
+BEST_SLT = {"schedule": "slt", "tile": (40, 112), "time_depth": 4, "cot_threshold": (2, 256, 256)}
+BATCH = {"tile": (96, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 
@@ -382,10 +384,12 @@ def compare_schedules(pcot, h, base, sizes, strides, stream):
     """Context numbers: the plain sweep, SLT and COT in FP32 (own workspaces)."""
     import torch
     out = {}
-    prm = pcot.tile_params(tile=BEST["tile"], time_depth=BEST["time_depth"], cot_threshold=BEST["cot_threshold"])
-    cot_prm = pcot.tile_params(tile=BEST_COT["tile"], time_depth=BEST_COT["time_depth"],
-                               cot_threshold=BEST_COT["cot_threshold"])
-    cases = [("sweep_f32", pcot.PCOT_SWEEP, None), ("slt_f32", pcot.PCOT_SLT, prm), ("cot_f32", pcot.PCOT_COT, cot_prm)]
+    slt_prm = pcot.tile_params(tile=BEST_SLT["tile"], time_depth=BEST_SLT["time_depth"],
+                               cot_threshold=BEST_SLT["cot_threshold"])
+    cot_prm = pcot.tile_params(tile=BEST["tile"], time_depth=BEST["time_depth"], cot_threshold=BEST["cot_threshold"])
+    cot_fine = pcot.tile_params(tile=(32, 112), time_depth=8, cot_threshold=(8, 8, 8))
+    cases = [("sweep_f32", pcot.PCOT_SWEEP, None), ("slt_f32", pcot.PCOT_SLT, slt_prm),
+             ("cot_f32", pcot.PCOT_COT, cot_prm), ("cot_f32_l2_leaves", pcot.PCOT_COT, cot_fine)]
     for name, sched, p in cases:
         nb = pcot.pcot_workspace_bytes(h, sizes, strides, T_STEPS, pcot.PCOT_F32, sched, p)
         ws = torch.empty(nb, dtype=torch.uint8, device="cuda")

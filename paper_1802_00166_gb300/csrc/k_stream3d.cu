@@ -1,13 +1,14 @@
 // 3-D tile kernel: trapezoid in (y, x), streamed along axis 0 (z).
 //
-// One CTA = NW warps stacked along y (one row each), every warp covering a
-// span of 64 contiguous x cells (two elements per lane).  Planes of the tile
-// stream through from z0-K to z0+Hz+K-1; stage s keeps its last three planes
-// of the lane's cells in a register ring, x-neighbours come from warp
-// shuffles and y-neighbours from a per-stage shared-memory plane written once
-// per z-step (double buffered, one barrier per step).  After K stages the
-// valid cells are the rows [K, NW-K) and the span minus K cells per side,
-// which is the tile's output (the overlapped/trapezoid tile of Sec. 3.3).
+// One CTA = NW warps stacked along y; each warp owns a brick of RY rows x 64
+// contiguous x cells (two elements per lane).  Planes of the tile stream
+// through from z0-K to z0+Hz+K-1; stage s keeps its last three planes of the
+// brick in a register ring, x-neighbours come from warp shuffles, y-neighbours
+// inside the brick from registers and across bricks from the brick edge rows
+// that every warp publishes in a per-stage shared-memory slot once per z-step
+// (double buffered, one barrier per z-step).  After K stages the valid cells
+// are the rows [K, NW*RY-K) and the span minus K cells per side, which is the
+// tile's output (the overlapped/trapezoid tile of Sec. 3.3).
 #include "tiled.cuh"
 
 namespace pcot {
@@ -16,8 +17,9 @@ namespace stream3d {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int E = 2;  // elements per lane
-constexpr int kMaxWarps = 32;
+constexpr int E = 2;    // elements per lane
+constexpr int RY = 4;   // rows per warp
+constexpr int kMaxWarps = 16;
 
 template <class T>
 struct V2;
@@ -36,6 +38,16 @@ struct Shape {
     static constexpr int Wo = 32 * E - 2 * Kp;
 };
 
+// Register budget per thread: the stage rings hold 3*K*RY*E values.
+template <class T, int K>
+constexpr int kRegBudget3 = sizeof(T) == 8 ? (K <= 1 ? 168 : 232) : (K <= 1 ? 96 : (K <= 2 ? 128 : 168));
+
+// Warps per CTA the budget allows within the 64K-register file.
+inline int max_warps_for(int dtype, int depth) {
+    if (dtype != kF32) return 8;
+    return depth <= 2 ? kMaxWarps : 12;
+}
+
 template <class T, bool EXACT, int K, bool CG>
 __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restrict__ dst, const DevGeo& g,
                                          const Coeffs<T>& c, int64_t z0, int64_t Hz, int64_t y0, int64_t Hy,
@@ -45,31 +57,39 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
+    const int NR = NW * RY;  // rows of the CTA
     const bool per = g.periodic != 0;
     const int64_t ez = g.e[0], ey = g.e[1], ex = g.e[2];
     const int64_t nz = g.n[0], ny = g.n[1], nx = g.n[2];
     const int64_t Pz = g.s[0], Py = g.s[1];
 
-    const int64_t y = y0 - K + w;  // storage row of this warp
+    const int64_t ybase = y0 - K + (int64_t)w * RY;  // storage row of the brick's first row
     const int64_t xl = x0 - Kp + (int64_t)lane * E;
     const int64_t xhi = x0 + Wx;
 
-    int64_t ysrc;
-    bool yin, yint;
-    if (per) {
-        ysrc = wrap_fast(y, ny);
-        yin = true;
-        yint = true;
-    } else {
-        ysrc = y;
-        yin = y >= 0 && y < ey;
-        yint = y >= 1 && y <= ny;
+    int64_t ysrc[RY];
+    bool yin[RY], yint[RY], ystore[RY];
+    bool brick_int = true;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const int64_t y = ybase + r;
+        if (per) {
+            ysrc[r] = wrap_fast(y, ny);
+            yin[r] = true;
+            yint[r] = true;
+        } else {
+            ysrc[r] = y;
+            yin[r] = y >= 0 && y < ey;
+            yint[r] = y >= 1 && y <= ny;
+        }
+        const int ry = w * RY + r;
+        ystore[r] = ry >= K && ry < NR - K && y < y0 + Hy && (per ? y < ny : yint[r]);
+        brick_int = brick_int && yint[r];
     }
-    const bool ystore = w >= K && w < NW - K && y < y0 + Hy && (per ? y < ny : yint);
 
-    bool inb[E], xint[E], st[E];
+    bool inb[E], xint[E], stx[E];
     int64_t col[E];
-    bool all_in = true, all_st = true, lane_xint = true;
+    bool all_in = true, all_stx = true, lane_xint = true;
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int64_t x = xl + j;
@@ -82,17 +102,17 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             inb[j] = x >= 0 && x < ex;
             xint[j] = x >= 1 && x <= nx;
         }
-        st[j] = ystore && x >= x0 && x < xhi && (per ? x < nx : xint[j]);
+        stx[j] = x >= x0 && x < xhi && (per ? x < nx : xint[j]);
         all_in = all_in && inb[j];
-        all_st = all_st && st[j];
+        all_stx = all_stx && stx[j];
         lane_xint = lane_xint && xint[j];
     }
     const bool lvec = vec_ok && all_in && col[1] == col[0] + 1 && (col[0] % E) == 0;
-    const bool svec = vec_ok && all_st && (xl % E) == 0;
+    const bool svec = vec_ok && all_stx && (xl % E) == 0;
     const bool warp_xint = __all_sync(kFull, lane_xint);
-    const bool row_ok = per || (yint && warp_xint);  // no pass-through needed on this row
+    const bool brick_ok = per || (brick_int && warp_xint);  // no pass-through inside this brick
 
-    auto load_plane = [&](int64_t zi, T (&v)[E]) {
+    auto load_row = [&](int64_t zi, int r, T (&v)[E]) {
         int64_t zs;
         bool zin;
         if (per) {
@@ -102,12 +122,12 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             zs = zi;
             zin = zi >= 0 && zi < ez;
         }
-        if (!zin || !yin) {
+        if (!zin || !yin[r]) {
             v[0] = T(0);
             v[1] = T(0);
             return;
         }
-        const T* rowp = src + zs * Pz + ysrc * Py;
+        const T* rowp = src + zs * Pz + ysrc[r] * Py;
         if (lvec) {
             const V q = gload<CG>(reinterpret_cast<const V*>(rowp + col[0]));
             v[0] = q.x;
@@ -118,81 +138,111 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         }
     };
 
-    // sm[buf][s][w][32*E]
-    const int rowlen = 32 * E;
-    const int stage_stride = NW * rowlen;
+    // sm[buf][s][w][edge][32*E]: edge 0 = the brick's first row, 1 = its last.
+    constexpr int rowlen = 32 * E;
+    const int warp_stride = 2 * rowlen;
+    const int stage_stride = NW * warp_stride;
     const int buf_stride = K * stage_stride;
 
-    T R[K][3][E];
+    T R[K][3][RY][E];
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
         for (int u = 0; u < 3; ++u)
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[s][u][j] = T(0);
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j) R[s][u][r][j] = T(0);
 
     const int64_t zbeg = z0 - K, zend = z0 + Hz + K;
-    T pf[3][E];  // three planes in flight per lane
-    load_plane(zbeg, pf[0]);
-    if (zbeg + 1 < zend) load_plane(zbeg + 1, pf[1]);
-    if (zbeg + 2 < zend) load_plane(zbeg + 2, pf[2]);
+    T pf[RY][E];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) load_row(zbeg, r, pf[r]);
     int buf = 0;
 
     auto step = [&](auto Uc, int64_t zi) {
         constexpr int U = decltype(Uc)::value;
         constexpr int SA = U % 3, SB = (U + 1) % 3, SN = (U + 2) % 3;
-        R[0][SN][0] = pf[U][0];
-        R[0][SN][1] = pf[U][1];
-        if (zi + 3 < zend) load_plane(zi + 3, pf[U]);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            R[0][SN][r][0] = pf[r][0];
+            R[0][SN][r][1] = pf[r][1];
+        }
+        if (zi + 1 < zend) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r) load_row(zi + 1, r, pf[r]);
+        }
         T* smb = sm + buf * buf_stride;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            V q;
-            q.x = R[s][SB][0];
-            q.y = R[s][SB][1];
-            *reinterpret_cast<V*>(smb + s * stage_stride + w * rowlen + lane * E) = q;
+            V q0, q1;
+            q0.x = R[s][SB][0][0];
+            q0.y = R[s][SB][0][1];
+            q1.x = R[s][SB][RY - 1][0];
+            q1.y = R[s][SB][RY - 1][1];
+            T* wp = smb + s * stage_stride + w * warp_stride + lane * E;
+            *reinterpret_cast<V*>(wp) = q0;
+            *reinterpret_cast<V*>(wp + rowlen) = q1;
         }
         __syncthreads();
-        T out[E];
+        T out[RY][E];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             const int64_t zr = zi - s - 1;  // plane of time level s+1 produced now
             const T* sp = smb + s * stage_stride + lane * E;
-            V nq, sq;
-            if (w > 0) nq = *reinterpret_cast<const V*>(sp + (w - 1) * rowlen);
-            else { nq.x = R[s][SB][0]; nq.y = R[s][SB][1]; }
-            if (w < NW - 1) sq = *reinterpret_cast<const V*>(sp + (w + 1) * rowlen);
-            else { sq.x = R[s][SB][0]; sq.y = R[s][SB][1]; }
-            const T wl = __shfl_up_sync(kFull, R[s][SB][1], 1);
-            const T er = __shfl_down_sync(kFull, R[s][SB][0], 1);
-            out[0] = upd3<T, EXACT>(c, R[s][SB][0], R[s][SA][0], R[s][SN][0], nq.x, sq.x, wl, R[s][SB][1]);
-            out[1] = upd3<T, EXACT>(c, R[s][SB][1], R[s][SA][1], R[s][SN][1], nq.y, sq.y, R[s][SB][0], er);
+            V nq, sq;  // row above the brick, row below the brick
+            if (w > 0) nq = *reinterpret_cast<const V*>(sp + (w - 1) * warp_stride + rowlen);
+            else { nq.x = R[s][SB][0][0]; nq.y = R[s][SB][0][1]; }
+            if (w < NW - 1) sq = *reinterpret_cast<const V*>(sp + (w + 1) * warp_stride);
+            else { sq.x = R[s][SB][RY - 1][0]; sq.y = R[s][SB][RY - 1][1]; }
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const T n0 = r > 0 ? R[s][SB][r - 1][0] : nq.x;
+                const T n1 = r > 0 ? R[s][SB][r - 1][1] : nq.y;
+                const T s0 = r < RY - 1 ? R[s][SB][r + 1][0] : sq.x;
+                const T s1 = r < RY - 1 ? R[s][SB][r + 1][1] : sq.y;
+                const T wl = __shfl_up_sync(kFull, R[s][SB][r][1], 1);
+                const T er = __shfl_down_sync(kFull, R[s][SB][r][0], 1);
+                out[r][0] = upd3<T, EXACT>(c, R[s][SB][r][0], R[s][SA][r][0], R[s][SN][r][0], n0, s0, wl,
+                                           R[s][SB][r][1]);
+                out[r][1] = upd3<T, EXACT>(c, R[s][SB][r][1], R[s][SA][r][1], R[s][SN][r][1], n1, s1,
+                                           R[s][SB][r][0], er);
+            }
             if (!per) {
                 const bool zint = zr >= 1 && zr <= nz;
-                if (!(zint && row_ok)) {
+                if (!(zint && brick_ok)) {
 #pragma unroll
-                    for (int j = 0; j < E; ++j)
-                        if (!(zint && yint && xint[j])) out[j] = R[s][SB][j];
+                    for (int r = 0; r < RY; ++r)
+#pragma unroll
+                        for (int j = 0; j < E; ++j)
+                            if (!(zint && yint[r] && xint[j])) out[r][j] = R[s][SB][r][j];
                 }
             }
             if (s + 1 < K) {
-                R[s + 1][SN][0] = out[0];
-                R[s + 1][SN][1] = out[1];
+#pragma unroll
+                for (int r = 0; r < RY; ++r) {
+                    R[s + 1][SN][r][0] = out[r][0];
+                    R[s + 1][SN][r][1] = out[r][1];
+                }
             }
         }
         const int64_t zo = zi - K;
         const bool zok = zo >= z0 && zo < z0 + Hz && (per ? zo < nz : (zo >= 1 && zo <= nz));
         if (zok) {
-            T* rowp = dst + zo * Pz + y * Py;
-            if (svec) {
-                V q;
-                q.x = out[0];
-                q.y = out[1];
-                *reinterpret_cast<V*>(rowp + xl) = q;
-            } else {
 #pragma unroll
-                for (int j = 0; j < E; ++j)
-                    if (st[j]) rowp[xl + j] = out[j];
+            for (int r = 0; r < RY; ++r) {
+                if (!ystore[r]) continue;
+                T* rowp = dst + zo * Pz + (ybase + r) * Py;
+                if (svec) {
+                    V q;
+                    q.x = out[r][0];
+                    q.y = out[r][1];
+                    *reinterpret_cast<V*>(rowp + xl) = q;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < E; ++j)
+                        if (stx[j]) rowp[xl + j] = out[r][j];
+                }
             }
         }
         buf ^= 1;
@@ -206,8 +256,8 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
 }
 
 template <class T, bool EXACT, int K>
-__global__ void __launch_bounds__(32 * kMaxWarps) slt_kernel(const T* __restrict__ src, T* __restrict__ dst,
-                                                             DevGeo g, Coeffs<T> c, TileGeo t, bool vec_ok) {
+__global__ void __maxnreg__((kRegBudget3<T, K>)) slt_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
+                                                       Coeffs<T> c, TileGeo t, bool vec_ok) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t ix = blockIdx.x, iy = blockIdx.y, iz = blockIdx.z;
     cta_tile<T, EXACT, K, false>(src, dst, g, c, iz * t.ext[0], t.ext[0], iy * t.ext[1], t.ext[1], ix * t.ext[2],
@@ -215,8 +265,8 @@ __global__ void __launch_bounds__(32 * kMaxWarps) slt_kernel(const T* __restrict
 }
 
 template <class T, bool EXACT, int K>
-__global__ void __launch_bounds__(32 * kMaxWarps) cot_kernel(T* buf0, T* buf1, DevGeo g, Coeffs<T> c, TileGeo t,
-                                                             bool vec_ok, CotDev q) {
+__global__ void __maxnreg__((kRegBudget3<T, K>)) cot_kernel(T* buf0, T* buf1, DevGeo g, Coeffs<T> c, TileGeo t,
+                                                       bool vec_ok, CotDev q) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_tile;
     for (;;) {
@@ -254,7 +304,7 @@ bool vec_aligned(const DevGeo& g, const void* a, const void* b) {
 
 template <class T>
 size_t smem_t(const TileGeo& t) {
-    return (size_t)2 * t.depth * t.nwarps * 32 * E * sizeof(T);
+    return (size_t)2 * t.depth * t.nwarps * 2 * 32 * E * sizeof(T);
 }
 
 template <class T, bool EXACT, int K>
@@ -316,13 +366,13 @@ bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t) {
     const int Kp = ((depth + E - 1) / E) * E;
     const int Wo = 32 * E - 2 * Kp;
     int64_t Hz = req && req[0] > 0 ? req[0] : 64;
-    int64_t Hy = req && req[1] > 0 ? req[1] : 32 - 2 * depth;
+    // Rows of a CTA = warps x RY, as many warps as the register budget allows.
+    const int maxw = max_warps_for(L.dtype, depth);
+    int64_t Hy = req && req[1] > 0 ? req[1] : 8 * RY - 2 * depth;
     if (Hy < depth) Hy = depth;
-    int nw = (int)Hy + 2 * depth;
-    if (nw > kMaxWarps) {
-        nw = kMaxWarps;
-        Hy = nw - 2 * depth;
-    }
+    int nw = (int)((Hy + 2 * depth + RY - 1) / RY);
+    if (nw > maxw) nw = maxw;
+    Hy = (int64_t)nw * RY - 2 * depth;
     if (Hy < depth) return false;
     if (Hz < depth) Hz = depth;
     // Tiles along x: as few warps as the span allows, extents balanced and

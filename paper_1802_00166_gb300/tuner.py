@@ -41,12 +41,13 @@ def candidates(dims, dtype, periodic):
     if dims == 2:
         ks = (2, 4, 6, 8) if dtype == S.PCOT_F32 else (1, 2, 4)
         for k in ks:
-            for H in (0, 64, 128, 256):
+            for H in (0, 48, 96):
                 out.append((S.PCOT_SLT, dict(tile=(H, 0), time_depth=k)))
         if not periodic:
-            for k in ((4, 8) if dtype == S.PCOT_F32 else (1, 2)):
-                for th in ((1, 1, 1), (2, 16, 64), (2, 64, 64), (4, 32, 64), (2, 256, 256)):
-                    out.append((S.PCOT_COT, dict(tile=(64, 0), time_depth=k, cot_threshold=th)))
+            for k in ((4, 6, 8) if dtype == S.PCOT_F32 else (1, 2)):
+                for H in (64, 96, 128):
+                    for th in ((2, 256, 256), (2, 64, 64), (4, 16, 16)):
+                        out.append((S.PCOT_COT, dict(tile=(H, 0), time_depth=k, cot_threshold=th)))
     elif dims == 3:
         ks = (1, 2, 3, 4) if dtype == S.PCOT_F32 else (1, 2)
         for k in ks:
@@ -67,7 +68,7 @@ def candidates(dims, dtype, periodic):
 def default_candidate(dims, dtype):
     """The method without the model: one fixed mid-range tile shape."""
     if dims == 2:
-        return (pcot.PCOT_SLT, dict(tile=(128, 0), time_depth=4 if dtype == pcot.PCOT_F32 else 1))
+        return (pcot.PCOT_SLT, dict(tile=(0, 0), time_depth=4 if dtype == pcot.PCOT_F32 else 1))
     if dims == 3:
         return (pcot.PCOT_SLT, dict(tile=(64, 0, 0), time_depth=2))
     return (pcot.PCOT_SLT, dict(tile=(32,), time_depth=16))
