@@ -22,6 +22,7 @@
 //    keeps three rows of 16-byte loads in flight in registers.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "tiled.cuh"
 #include "tma.cuh"
@@ -41,6 +42,21 @@ struct Shape {
     static constexpr int Kp = ((K + E - 1) / E) * E;   // halo rounded to whole lanes
     static constexpr int Wo = 32 * E - 2 * Kp;          // output columns per warp
 };
+
+// Interior FP32 warps fed by TMA evaluate the update two cells at a time with the packed
+// f32x2 multiply and fused multiply-add (same per-cell rounding and operand
+// order as the scalar path, so the results are bitwise unchanged).  A lane's
+// four columns c0..c3 are stored as the pairs (c0, c2) and (c1, c3): then the
+// west neighbours of (c1, c3) and the east neighbours of (c0, c2) are existing
+// pairs, and only (w, c1) and (c2, e) have to be assembled per stage.
+template <class T, bool EXACT, bool CHECK, bool TMA>
+constexpr bool kPacked = std::is_same<T, float>::value && !EXACT && !CHECK && TMA;
+
+// Register slot of lane column j (identity unless packed).
+template <bool PK>
+__device__ __forceinline__ constexpr int slot_of(int j) {
+    return PK ? (j == 1 ? 2 : j == 2 ? 1 : j) : j;
+}
 
 template <class T>
 struct Args {
@@ -165,6 +181,12 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     }
     const bool warp_xint = __all_sync(kFull, xint[0] && xint[E - 1]);
 
+    constexpr bool PK = kPacked<T, EXACT, CHECK, TMA>;
+    static_assert(!PK || E == 4, "packed path assumes four columns per lane");
+    float2 k2[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) k2[c] = make_float2((float)A.c.c[c], (float)A.c.c[c]);
+
     T R[K][3][E];
 #pragma unroll
     for (int s = 0; s < K; ++s)
@@ -210,22 +232,44 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             const V q = *reinterpret_cast<const V*>(ring + (lane_ring + slot * A.slot_elems + r * A.BW));
             const T* qq = reinterpret_cast<const T*>(&q);
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][j] = qq[j];
+            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
         } else {
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][j] = pf[U][j];
+            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = pf[U][j];
             if (i + 3 < nrows) load_row(ybeg + i + 3, pf[U]);
         }
         T out[E];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            const T wl = __shfl_up_sync(kFull, R[s][SB][E - 1], 1);
-            const T er = __shfl_down_sync(kFull, R[s][SB][0], 1);
+            if constexpr (PK) {
+                // slots: 0 = c0, 1 = c2, 2 = c1, 3 = c3
+                const float wl = __shfl_up_sync(kFull, R[s][SB][3], 1);    // c3 of the lane to the west
+                const float er = __shfl_down_sync(kFull, R[s][SB][0], 1);  // c0 of the lane to the east
+                const float2 cA = make_float2(R[s][SB][0], R[s][SB][1]);   // (c0, c2)
+                const float2 cB = make_float2(R[s][SB][2], R[s][SB][3]);   // (c1, c3)
+                float2 oA = __fmul2_rn(k2[0], cA);
+                oA = __ffma2_rn(k2[1], make_float2(R[s][SA][0], R[s][SA][1]), oA);
+                oA = __ffma2_rn(k2[2], make_float2(R[s][SN][0], R[s][SN][1]), oA);
+                oA = __ffma2_rn(k2[3], make_float2(wl, R[s][SB][2]), oA);   // west of (c0, c2)
+                oA = __ffma2_rn(k2[4], cB, oA);                              // east of (c0, c2)
+                float2 oB = __fmul2_rn(k2[0], cB);
+                oB = __ffma2_rn(k2[1], make_float2(R[s][SA][2], R[s][SA][3]), oB);
+                oB = __ffma2_rn(k2[2], make_float2(R[s][SN][2], R[s][SN][3]), oB);
+                oB = __ffma2_rn(k2[3], cA, oB);                              // west of (c1, c3)
+                oB = __ffma2_rn(k2[4], make_float2(R[s][SB][1], er), oB);   // east of (c1, c3)
+                out[0] = oA.x;
+                out[1] = oA.y;
+                out[2] = oB.x;
+                out[3] = oB.y;
+            } else {
+                const T wl = __shfl_up_sync(kFull, R[s][SB][E - 1], 1);
+                const T er = __shfl_down_sync(kFull, R[s][SB][0], 1);
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const T W = j > 0 ? R[s][SB][j - 1] : wl;
-                const T Ea = j < E - 1 ? R[s][SB][j + 1] : er;
-                out[j] = upd2<T, EXACT>(A.c, R[s][SB][j], R[s][SA][j], R[s][SN][j], W, Ea);
+                for (int j = 0; j < E; ++j) {
+                    const T W = j > 0 ? R[s][SB][j - 1] : wl;
+                    const T Ea = j < E - 1 ? R[s][SB][j + 1] : er;
+                    out[j] = upd2<T, EXACT>(A.c, R[s][SB][j], R[s][SA][j], R[s][SN][j], W, Ea);
+                }
             }
             if constexpr (CHECK) {
                 const int rr = i - s - 1;
@@ -254,12 +298,12 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 V q;
                 T* qq = reinterpret_cast<T*>(&q);
 #pragma unroll
-                for (int j = 0; j < E; ++j) qq[j] = out[j];
+                for (int j = 0; j < E; ++j) qq[j] = out[slot_of<PK>(j)];
                 *reinterpret_cast<V*>(rowp) = q;
             } else {
 #pragma unroll
                 for (int j = 0; j < E; ++j)
-                    if (st[j]) rowp[j] = out[j];
+                    if (st[j]) rowp[j] = out[slot_of<PK>(j)];
             }
         }
     };

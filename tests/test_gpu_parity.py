@@ -109,6 +109,27 @@ def test_heat2d_f32_within_tolerance(sched, k):
     pcot.pcot_destroy(h)
 
 
+@pytest.mark.parametrize("sched", [pcot.PCOT_SLT, pcot.PCOT_COT])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8])
+def test_heat2d_f32_packed_equals_scalar(sched, k):
+    """Rows padded to 128 bytes take the TMA-fed tile, whose interior warps
+    update two cells per packed f32x2 instruction; unpadded rows take the
+    plain-load tile with scalar FMAs.  Both apply the same rounded operations
+    in the same order, so the FP32 results agree bitwise (and with the oracle
+    within the FP32 tolerance)."""
+    h = _handle(2)
+    sizes = (190, 517)
+    g32 = si.uniform_grid(sizes, 12, dtype=np.float32)
+    T = 41
+    p = pcot.tile_params(tile=(24, 0), time_depth=k, cot_threshold=(2, 2, 2))
+    scalar = run_gpu(h, g32, sizes, T, pcot.PCOT_F32, sched, p)
+    packed = run_gpu(h, g32, sizes, T, pcot.PCOT_F32, sched, p, strides=padded_strides(g32.shape, 4, 128))
+    assert np.array_equal(packed, scalar)
+    ref = oracle.sweep(g32, sizes, HEAT2D, T)
+    assert oracle.max_rel_error(oracle.interior(packed, sizes), oracle.interior(ref, sizes)) <= F32_TOL
+    pcot.pcot_destroy(h)
+
+
 def test_heat2d_periodic():
     h = _handle(2, periodic=True)
     sizes = (64, 256)
