@@ -157,6 +157,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over all ranks (a job takes as long as its slowest
+    rank); the value itself on a single process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of replicated work: the units every rank
+    processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -251,13 +268,9 @@ def run_gpu(args):
     st = pcot.pcot_check(h, stream)
     if st != pcot.PCOT_OK:
         raise pcot.PcotError(st, "timed region")
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     updates = float(N_SIDE * N_SIDE * T_STEPS)
-    value = updates * args.steps * ws / (ms / 1e3) / 1e9
+    value = job_rate(updates * args.steps, ws, ms / 1e3) / 1e9
 
     # End to end through the host-buffer entry point (pinned host grid, the
     # H2D copy, the run and the D2H copy inside each timed step).
@@ -265,13 +278,15 @@ def run_gpu(args):
     host.copy_(base.cpu())
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         pcot.pcot_run_host(h, host.data_ptr(), base.data_ptr(), wsbuf.data_ptr(), nb, sizes, strides, T_STEPS,
                            pcot.PCOT_F32, sched, params, stream)
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     span = (shape[0] - 1) * pitch + shape[1]
-    e2e = {"value": updates * e2e_steps * ws / e2e_dt / 1e9, "unit": UNIT,
+    e2e = {"value": job_rate(updates * e2e_steps, ws, e2e_dt) / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": span * 4, "d2h_bytes_per_step": span * 4}
 
     # Roofline of the dominant kernel.  The temporal-blocking model charges one

@@ -1,0 +1,80 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks.
+
+The method has no exchange step between GPUs (each rank advances its own
+replica of the grid), so the only cross-rank operations are the barrier and
+the max-over-ranks of the timed durations.  These run here as two processes
+on the gloo backend; the reference arm's rule that only rank 0 runs and
+prints is checked in-process."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+_RANK_BODY = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo", init_method="env://")
+rank, world = dist.get_rank(), dist.get_world_size()
+local_seconds = 1.5 + rank            # rank 1 is the slow one
+dist.barrier()
+slowest = bench.max_over_ranks(local_seconds, dist, "cpu")
+assert slowest == 1.5 + (world - 1), slowest
+rate = bench.job_rate(1000.0, world, slowest)
+assert abs(rate - 1000.0 * world / slowest) < 1e-9
+print("rank", rank, "ok", slowest, rate, flush=True)
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_max_over_ranks_and_job_rate_gloo_world2():
+    pytest.importorskip("torch")
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2",
+                   LOCAL_RANK=str(rank))
+        procs.append(subprocess.Popen([sys.executable, "-c", _RANK_BODY.format(root=ROOT)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        try:
+            out, err = p.communicate(timeout=120)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            out, err = p.communicate()
+        outs.append((p.returncode, out, err))
+    for rank, (rc, out, err) in enumerate(outs):
+        assert rc == 0, (rank, out, err[-2000:])
+        assert f"rank {rank} ok 2.5" in out
+
+
+def test_single_process_values_pass_through():
+    import bench
+    assert bench.max_over_ranks(3.25) == 3.25
+    assert bench.job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
+    """Under torchrun every rank but 0 exits at once, without work or output."""
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    class Args:
+        steps, warmup = 1, 3
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""
