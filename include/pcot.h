@@ -26,7 +26,9 @@
  * ---------------------------------------
  *  Coefficients: ncoeffs = 1 + 2*dims*radius doubles, ordered centre, then
  *    axis 0 (slowest) .. axis dims-1 (fastest); per axis offsets -r..-1 then
- *    +1..+r.  The update accumulates in exactly that order.
+ *    +1..+r.  PCOT_F64_EXACT accumulates in exactly that order; the FMA
+ *    modes (PCOT_F32, PCOT_F64) accumulate the same terms with the axis-0
+ *    +1 neighbour moved last (see Precision).
  *  Grid layout: row-major, the last axis contiguous (stride 1).  `sizes` are
  *    the INTERIOR sizes n_a.  Dirichlet grids store n_a + 2r entries per axis;
  *    the outer ring of width r holds fixed boundary values that are never
@@ -35,8 +37,11 @@
  *    the contiguous layout.  A padded pitch whose byte size is a multiple of
  *    16 (and a 16-byte-aligned base) lets the kernels use 16-byte vector
  *    accesses; other layouts are accepted and run with narrower accesses.
- *  Precision: PCOT_F32 grids hold float and may use fused multiply-add;
- *    PCOT_F64 grids hold double and may use fused multiply-add;
+ *  Precision: PCOT_F32 grids hold float and use fused multiply-add;
+ *    PCOT_F64 grids hold double and use fused multiply-add; in both, every
+ *    schedule evaluates a point with the same operations in the same order
+ *    (centre product first, the axis-0 +1 term last), so the schedules agree
+ *    with each other bitwise and with the exact definition within rounding;
  *    PCOT_F64_EXACT grids hold double and use separately rounded multiply and
  *    add in the order above, so results are bitwise identical to a plain
  *    IEEE-754 binary64 evaluation of the definition.

@@ -49,7 +49,11 @@ struct Arith<float, false> {
     static __device__ __forceinline__ float acc(float a, float c, float u) { return __fmaf_rn(c, u, a); }
 };
 
-// Star update in coefficient order: centre, then (minus, plus) per axis.
+// Star update.  FP64 exact mode adds in coefficient order: centre, then
+// (minus, plus) per axis.  The FMA modes add the axis-0 plus neighbour last:
+// the tile kernels stream along axis 0, so that operand is the row (plane)
+// the previous stage has just produced, and putting it last leaves a single
+// dependent FMA between consecutive stages of one step.
 template <class T, bool EXACT>
 __device__ __forceinline__ T upd1(const Coeffs<T>& c, T C, T m0, T p0) {
     using A = Arith<T, EXACT>;
@@ -63,9 +67,15 @@ __device__ __forceinline__ T upd2(const Coeffs<T>& c, T C, T m0, T p0, T m1, T p
     using A = Arith<T, EXACT>;
     T a = A::first(c.c[0], C);
     a = A::acc(a, c.c[1], m0);
-    a = A::acc(a, c.c[2], p0);
-    a = A::acc(a, c.c[3], m1);
-    a = A::acc(a, c.c[4], p1);
+    if constexpr (EXACT) {
+        a = A::acc(a, c.c[2], p0);
+        a = A::acc(a, c.c[3], m1);
+        a = A::acc(a, c.c[4], p1);
+    } else {
+        a = A::acc(a, c.c[3], m1);
+        a = A::acc(a, c.c[4], p1);
+        a = A::acc(a, c.c[2], p0);
+    }
     return a;
 }
 template <class T, bool EXACT>
@@ -73,11 +83,19 @@ __device__ __forceinline__ T upd3(const Coeffs<T>& c, T C, T m0, T p0, T m1, T p
     using A = Arith<T, EXACT>;
     T a = A::first(c.c[0], C);
     a = A::acc(a, c.c[1], m0);
-    a = A::acc(a, c.c[2], p0);
-    a = A::acc(a, c.c[3], m1);
-    a = A::acc(a, c.c[4], p1);
-    a = A::acc(a, c.c[5], m2);
-    a = A::acc(a, c.c[6], p2);
+    if constexpr (EXACT) {
+        a = A::acc(a, c.c[2], p0);
+        a = A::acc(a, c.c[3], m1);
+        a = A::acc(a, c.c[4], p1);
+        a = A::acc(a, c.c[5], m2);
+        a = A::acc(a, c.c[6], p2);
+    } else {
+        a = A::acc(a, c.c[3], m1);
+        a = A::acc(a, c.c[4], p1);
+        a = A::acc(a, c.c[5], m2);
+        a = A::acc(a, c.c[6], p2);
+        a = A::acc(a, c.c[2], p0);
+    }
     return a;
 }
 

@@ -150,11 +150,8 @@ __global__ void __launch_bounds__(kThreads) cot_kernel(T* buf0, T* buf1, DevGeo 
         const T* src = (b & 1) ? buf1 : buf0;
         T* dst = (b & 1) ? buf0 : buf1;
         tile_body<T, EXACT, DIMS, true>(src, dst, g, c, o, w, t.depth, reinterpret_cast<T*>(smraw));
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            release_successors(q, DIMS, b, ii[0], ii[1], ii[2]);
-        }
+        __syncthreads();  // the tile's stores by every thread precede thread 0's release
+        if (threadIdx.x == 0) release_successors(q, DIMS, b, ii[0], ii[1], ii[2]);
     }
 }
 

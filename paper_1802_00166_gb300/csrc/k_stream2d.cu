@@ -247,16 +247,18 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 const float er = __shfl_down_sync(kFull, R[s][SB][0], 1);  // c0 of the lane to the east
                 const float2 cA = make_float2(R[s][SB][0], R[s][SB][1]);   // (c0, c2)
                 const float2 cB = make_float2(R[s][SB][2], R[s][SB][3]);   // (c1, c3)
+                // operand order of upd2 in the FMA modes: the south row (this
+                // step's output of the previous stage) enters last
                 float2 oA = __fmul2_rn(k2[0], cA);
                 oA = __ffma2_rn(k2[1], make_float2(R[s][SA][0], R[s][SA][1]), oA);
-                oA = __ffma2_rn(k2[2], make_float2(R[s][SN][0], R[s][SN][1]), oA);
                 oA = __ffma2_rn(k2[3], make_float2(wl, R[s][SB][2]), oA);   // west of (c0, c2)
                 oA = __ffma2_rn(k2[4], cB, oA);                              // east of (c0, c2)
+                oA = __ffma2_rn(k2[2], make_float2(R[s][SN][0], R[s][SN][1]), oA);
                 float2 oB = __fmul2_rn(k2[0], cB);
                 oB = __ffma2_rn(k2[1], make_float2(R[s][SA][2], R[s][SA][3]), oB);
-                oB = __ffma2_rn(k2[2], make_float2(R[s][SN][2], R[s][SN][3]), oB);
                 oB = __ffma2_rn(k2[3], cA, oB);                              // west of (c1, c3)
                 oB = __ffma2_rn(k2[4], make_float2(R[s][SB][1], er), oB);   // east of (c1, c3)
+                oB = __ffma2_rn(k2[2], make_float2(R[s][SN][2], R[s][SN][3]), oB);
                 out[0] = oA.x;
                 out[1] = oA.y;
                 out[2] = oB.x;
@@ -391,12 +393,24 @@ __device__ __forceinline__ void init_ring(const SmemRing<T>& r, int nwarps) {
     __syncthreads();
 }
 
-// Register budget of a K-stage tile (the stage rings hold 3*K*E values).
-template <int K>
-constexpr int kRegBudget = K >= 8 ? 184 : (K >= 6 ? 160 : 128);
+// Register budgets (registers per thread) of the K-stage tile kernels; the
+// stage rings hold 3*K*E values.  The kernels are latency-bound, so resident
+// warps matter: with one-warp CTAs an SM holds floor(2048 / budget) of them.
+// The FP32 TMA-fed variants (the fast path) get budgets just above their
+// spill-free minimum, per kernel; the others keep roomier ones.
+enum class Kern { Slt, Cot, Batch };
+template <Kern W, class T, int K, bool TMA>
+constexpr int reg_budget() {
+    if (std::is_same<T, float>::value && TMA) {
+        if (W == Kern::Slt) return K >= 8 ? 184 : K >= 6 ? 160 : 128;
+        if (W == Kern::Cot) return K >= 8 ? 184 : K >= 6 ? 160 : 128;
+        return K >= 8 ? 184 : K >= 6 ? 160 : 128;
+    }
+    return K >= 8 ? 184 : (K >= 6 ? 160 : 128);
+}
 
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __maxnreg__(kRegBudget<K>) slt_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __maxnreg__((reg_budget<Kern::Slt, T, K, TMA>())) slt_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(128) unsigned char smraw[];
     constexpr int Wo = Shape<K, Vec<T>::E>::Wo;
     constexpr int Kp = Shape<K, Vec<T>::E>::Kp;
@@ -419,7 +433,7 @@ __global__ void __maxnreg__(kRegBudget<K>) slt_kernel(Args<T> A, const __grid_co
 }
 
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __maxnreg__(kRegBudget<K>) cot_kernel(Args<T> A, T* buf0, T* buf1, CotDev q,
+__global__ void __maxnreg__((reg_budget<Kern::Cot, T, K, TMA>())) cot_kernel(Args<T> A, T* buf0, T* buf1, CotDev q,
                                                              const __grid_constant__ CUtensorMap map0,
                                                              const __grid_constant__ CUtensorMap map1) {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -464,11 +478,8 @@ __global__ void __maxnreg__(kRegBudget<K>) cot_kernel(Args<T> A, T* buf0, T* buf
                 warp_tile_any<T, EXACT, K, true, false>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi, 0,
                                                         0);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            release_successors(q, 2, b, iy, ix, 0);
-        }
+        __syncthreads();  // the tile's stores by every thread precede thread 0's release
+        if (threadIdx.x == 0) release_successors(q, 2, b, iy, ix, 0);
     }
 }
 
@@ -622,7 +633,7 @@ int occ_k(const LaunchCtx& L, const TileGeo& t) {
 
 // Persistent kernel over the merged tile queue of a batch of grids.
 template <class T, bool EXACT, int K, bool TMA>
-__global__ void __maxnreg__(kRegBudget<K>) batch_kernel(BatchDev q, Coeffs<T> c) {
+__global__ void __maxnreg__((reg_budget<Kern::Batch, T, K, TMA>())) batch_kernel(BatchDev q, Coeffs<T> c) {
     extern __shared__ __align__(128) unsigned char smraw[];
     constexpr int E = Vec<T>::E;
     constexpr int Wo = Shape<K, E>::Wo;
@@ -660,8 +671,7 @@ __global__ void __maxnreg__(kRegBudget<K>) batch_kernel(BatchDev q, Coeffs<T> c)
                 } else if (!wait_zero(q.counts + q.desc[g].count_base + local, q.status, q.timeout_ns, local, pos)) {
                     g = -1;
                 }
-                __threadfence();
-                fence_proxy_async_global();
+                fence_proxy_async_global();  // TMA reads after the acquire of the counter
             }
             s_g = g;
             s_local = local;
@@ -711,9 +721,8 @@ __global__ void __maxnreg__(kRegBudget<K>) batch_kernel(BatchDev q, Coeffs<T> c)
                 warp_tile_any<T, EXACT, 1, true, false, Kp>(B, nullptr, nullptr, nullptr, nullptr, nwarps, y0, olo, ohi,
                                                             0, 0);
         }
-        __syncthreads();
+        __syncthreads();  // the tile's stores by every thread precede thread 0's release
         if (threadIdx.x == 0) {
-            __threadfence();
             if (b + 1 < d.Ptotal) {
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int jy = iy + dy;

@@ -286,11 +286,8 @@ __global__ void __maxnreg__((kRegBudget3<T, K>)) cot_kernel(T* buf0, T* buf1, De
         T* dst = (b & 1) ? buf0 : buf1;
         cta_tile<T, EXACT, K, true>(src, dst, g, c, (int64_t)iz * t.ext[0], t.ext[0], (int64_t)iy * t.ext[1],
                                     t.ext[1], (int64_t)ix * t.ext[2], t.ext[2], vec_ok, reinterpret_cast<T*>(smraw));
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            release_successors(q, 3, b, iz, iy, ix);
-        }
+        __syncthreads();  // the tile's stores by every thread precede thread 0's release
+        if (threadIdx.x == 0) release_successors(q, 3, b, iz, iy, ix);
     }
 }
 

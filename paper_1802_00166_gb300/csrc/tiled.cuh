@@ -34,6 +34,9 @@ inline Coeffs<T> coeffs_as(const double* c) {
 
 // Release the dependency counters of the successors of lattice tile
 // (b, i0, i1, i2): every (b+1, j) with |j_a - i_a| <= 1 inside the lattice.
+// Called by thread 0 after a CTA barrier: each red.release.gpu is cumulative,
+// so the tile's stores by all threads of the CTA (ordered before the barrier)
+// are visible to a CTA that observes the decrement with ld.acquire.gpu.
 __device__ __forceinline__ void release_successors(const CotDev& q, int dims, int b, int i0, int i1, int i2) {
     if (b + 1 >= q.lattice[0]) return;
     const int L0 = q.lattice[1], L1 = q.lattice[2], L2 = q.lattice[3];
@@ -60,8 +63,7 @@ __device__ __forceinline__ int pop_and_wait(const CotDev& q) {
     if (pos >= q.ntiles) return -1;
     const int tile = q.queue[pos];
     if (!wait_zero(q.counts + tile, q.status, q.timeout_ns, tile, pos)) return -1;
-    __threadfence();
-    return tile;
+    return tile;  // wait_zero's ld.acquire.gpu orders this CTA's later reads (after the CTA barrier)
 }
 
 // ---- batched persistent launch (many 2-D grids, one kernel) -------------

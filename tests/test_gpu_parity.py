@@ -130,6 +130,33 @@ def test_heat2d_f32_packed_equals_scalar(sched, k):
     pcot.pcot_destroy(h)
 
 
+@pytest.mark.parametrize("dims,sizes,periodic", [(1, (1000,), False), (2, (190, 517), False),
+                                                 (2, (64, 256), True), (3, (20, 33, 70), False),
+                                                 (3, (24, 16, 64), True)])
+@pytest.mark.parametrize("dtype", [pcot.PCOT_F32, pcot.PCOT_F64])
+def test_fma_modes_schedules_agree_bitwise(dims, sizes, periodic, dtype):
+    """In the FMA modes every kernel evaluates a point with the same rounded
+    operations in the same order, so the sweep, the single-level and the
+    recursive schedules (and the packed FP32 tile) give identical bits."""
+    h = _handle(dims, periodic=periodic)
+    g = si.uniform_grid(sizes, 21, periodic=periodic, dtype=np.float32 if dtype == pcot.PCOT_F32 else np.float64)
+    T = 23
+    tile = {1: (32,), 2: (24, 0), 3: (8, 0, 0)}[dims]
+    ref = run_gpu(h, g, sizes, T, dtype, pcot.PCOT_SWEEP)
+    runs = [(pcot.PCOT_SLT, k) for k in ((1, 2, 3, 4) if dims > 1 else (4, 16))]
+    if not periodic:
+        runs += [(pcot.PCOT_COT, k) for k in ((2, 4) if dims > 1 else (8,))]
+    elem = 4 if dtype == pcot.PCOT_F32 else 8
+    for sched, k in runs:
+        p = pcot.tile_params(tile=tile, time_depth=k, cot_threshold=(2, 2, 2, 2)[:dims + 1])
+        got = run_gpu(h, g, sizes, T, dtype, sched, p)
+        assert np.array_equal(got, ref), (sched, k)
+        if dims == 2:
+            got = run_gpu(h, g, sizes, T, dtype, sched, p, strides=padded_strides(g.shape, elem, 128))
+            assert np.array_equal(got, ref), (sched, k, "padded")
+    pcot.pcot_destroy(h)
+
+
 def test_heat2d_periodic():
     h = _handle(2, periodic=True)
     sizes = (64, 256)
