@@ -143,6 +143,13 @@ __device__ __forceinline__ void red_release_add_gpu(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Relaxed GPU-scope add: after one fence.acq_rel.gpu (__threadfence) a run of
+// these forms a release pattern for every counter, at the cost of one fence
+// instead of one per counter.
+__device__ __forceinline__ void red_relaxed_add_gpu(int* p, int v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Device status block written by kernels and read by pcot_check.
 struct DevStatus {
     int code;      // 0 ok, otherwise a pcot_status value

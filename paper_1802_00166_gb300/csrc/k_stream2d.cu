@@ -396,13 +396,15 @@ __device__ __forceinline__ void init_ring(const SmemRing<T>& r, int nwarps) {
 // Register budgets (registers per thread) of the K-stage tile kernels; the
 // stage rings hold 3*K*E values.  The kernels are latency-bound, so resident
 // warps matter: with one-warp CTAs an SM holds floor(2048 / budget) of them.
-// The FP32 TMA-fed variants (the fast path) get budgets just above their
-// spill-free minimum, per kernel; the others keep roomier ones.
+// Measured on Heat-2D 8192^2: the single-level kernel gains 4-13% from
+// budgets near its spill-free minimum (more resident warps); the persistent
+// kernels lose with them (the compiler's schedule under a tight budget costs
+// more than the extra warps give), so they keep the roomier budgets.
 enum class Kern { Slt, Cot, Batch };
 template <Kern W, class T, int K, bool TMA>
 constexpr int reg_budget() {
     if (std::is_same<T, float>::value && TMA) {
-        if (W == Kern::Slt) return K >= 8 ? 184 : K >= 6 ? 160 : 128;
+        if (W == Kern::Slt) return K >= 8 ? 152 : K >= 6 ? 120 : K >= 4 ? 96 : 128;
         if (W == Kern::Cot) return K >= 8 ? 184 : K >= 6 ? 160 : 128;
         return K >= 8 ? 184 : K >= 6 ? 160 : 128;
     }
@@ -723,6 +725,7 @@ __global__ void __maxnreg__((reg_budget<Kern::Batch, T, K, TMA>())) batch_kernel
         }
         __syncthreads();  // the tile's stores by every thread precede thread 0's release
         if (threadIdx.x == 0) {
+            __threadfence();  // one fence, then relaxed decrements: a release pattern
             if (b + 1 < d.Ptotal) {
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int jy = iy + dy;
@@ -735,7 +738,7 @@ __global__ void __maxnreg__((reg_budget<Kern::Batch, T, K, TMA>())) batch_kernel
                             atomicCAS(&q.status->code, 0, kStatusBounds);
                             continue;
                         }
-                        red_release_add_gpu(q.counts + d.count_base + succ, -1);
+                        red_relaxed_add_gpu(q.counts + d.count_base + succ, -1);
                     }
                 }
             }

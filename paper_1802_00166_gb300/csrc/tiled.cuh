@@ -34,11 +34,14 @@ inline Coeffs<T> coeffs_as(const double* c) {
 
 // Release the dependency counters of the successors of lattice tile
 // (b, i0, i1, i2): every (b+1, j) with |j_a - i_a| <= 1 inside the lattice.
-// Called by thread 0 after a CTA barrier: each red.release.gpu is cumulative,
-// so the tile's stores by all threads of the CTA (ordered before the barrier)
-// are visible to a CTA that observes the decrement with ld.acquire.gpu.
+// Called by thread 0 after a CTA barrier: one fence.acq_rel.gpu followed by
+// relaxed reductions is a release pattern (cumulative), so the tile's stores
+// by all threads of the CTA (ordered before the barrier) are visible to a CTA
+// that observes a decrement with ld.acquire.gpu.  One fence per tile instead
+// of one per counter: a fence waits for this SM's outstanding stores.
 __device__ __forceinline__ void release_successors(const CotDev& q, int dims, int b, int i0, int i1, int i2) {
     if (b + 1 >= q.lattice[0]) return;
+    __threadfence();
     const int L0 = q.lattice[1], L1 = q.lattice[2], L2 = q.lattice[3];
     for (int d0 = -1; d0 <= 1; ++d0) {
         const int j0 = i0 + d0;
@@ -50,7 +53,7 @@ __device__ __forceinline__ void release_successors(const CotDev& q, int dims, in
                 const int j2 = i2 + d2;
                 if (j2 < 0 || j2 >= L2) continue;
                 const int id = (((b + 1) * L0 + j0) * L1 + j1) * L2 + j2;
-                red_release_add_gpu(q.counts + id, -1);
+                red_relaxed_add_gpu(q.counts + id, -1);
             }
         }
     }
