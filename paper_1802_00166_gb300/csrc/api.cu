@@ -319,6 +319,14 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes
         q.timeout_ns = h->timeout_ns;
         int per_sm = cot_ctas_per_sm(L, c->tg);
         int64_t nctas = (int64_t)per_sm * h->num_sms;
+        // A tile of block b+1 depends on tiles about one block's worth of
+        // queue entries earlier; with more CTAs in flight than ~2/5 of a
+        // block, popped tiles find their predecessors still running and wait.
+        // Measured on Heat-2D 4096^2..8192^2: 2.5 tiles of a block per CTA is
+        // neutral on the large grid and 9-18% faster on the smaller ones.
+        const int64_t per_block = (int64_t)c->lattice[1] * c->lattice[2] * c->lattice[3];
+        const int64_t cap = std::max<int64_t>(h->num_sms, per_block * 2 / 5);
+        if (nctas > cap) nctas = cap;
         if (nctas > c->ntiles) nctas = c->ntiles;
         if (nctas < 1) nctas = 1;
         PCOT_CUDA(launch_cot(L, c->tg, grid, twin, q, (int)nctas));

@@ -45,7 +45,7 @@ def candidates(dims, dtype, periodic):
                 out.append((S.PCOT_SLT, dict(tile=(H, 0), time_depth=k)))
         if not periodic:
             for k in ((4, 6, 8) if dtype == S.PCOT_F32 else (1, 2)):
-                for H in (64, 96, 128):
+                for H in (64, 80, 96, 128):
                     for th in ((2, 256, 256), (2, 64, 64), (4, 16, 16)):
                         out.append((S.PCOT_COT, dict(tile=(H, 0), time_depth=k, cot_threshold=th)))
     elif dims == 3:
