@@ -157,6 +157,67 @@ def _dist():
     return ws, rank, local
 
 
+class EnergyMeter:
+    """The GPU's total-energy counter (NVML, millijoules since driver load),
+    read through the driver's own libnvidia-ml with ctypes.  Reads only; no
+    setting of the GPU is touched.  `ok` is False where NVML is missing."""
+
+    def __init__(self, index=0, pci_bus_id=None, lib=None):
+        import ctypes
+        self.ct = ctypes
+        self.ok = False
+        try:
+            self.nvml = lib if lib is not None else ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            rc = 1
+            if pci_bus_id:
+                rc = self.nvml.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(h))
+            if rc != 0:
+                rc = self.nvml.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h))
+            if rc != 0:
+                return
+            self.h = h
+            self.ok = self.read_mj() is not None
+        except Exception:
+            self.ok = False
+
+    def read_mj(self):
+        e = self.ct.c_ulonglong(0)
+        try:
+            if self.nvml.nvmlDeviceGetTotalEnergyConsumption(self.h, self.ct.byref(e)) != 0:
+                return None
+        except Exception:
+            return None
+        return int(e.value)
+
+
+def energy_per_update_nj(meter, run, sync, updates_per_run, min_seconds=1.5):
+    """Joules the GPU drew over repeated runs, per point update, in nJ (None
+    without a meter).  Runs for at least `min_seconds` so the counter's update
+    period is small against the interval."""
+    if meter is None or not meter.ok:
+        return None
+    run()
+    sync()
+    t0 = time.perf_counter()
+    run()
+    sync()
+    n = max(2, int(min_seconds / max(time.perf_counter() - t0, 1e-4)) + 1)
+    e0 = meter.read_mj()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        run()
+    sync()
+    dt = time.perf_counter() - t0
+    e1 = meter.read_mj()
+    if e0 is None or e1 is None or e1 <= e0:
+        return None
+    return {"nJ_per_update": (e1 - e0) * 1e-3 / (updates_per_run * n) * 1e9, "avg_W": (e1 - e0) * 1e-3 / dt,
+            "runs": n, "seconds": dt}
+
+
 def max_over_ranks(value, dist=None, device="cpu"):
     """The largest value over all ranks (a job takes as long as its slowest
     rank); the value itself on a single process."""
@@ -415,9 +476,19 @@ def run_batched(pcot, stream, steps):
 
 
 def compare_schedules(pcot, h, base, sizes, strides, stream):
-    """Context numbers: the plain sweep, SLT and COT in FP32 (own workspaces)."""
+    """Context numbers: the plain sweep, SLT and COT in FP32 (own workspaces),
+    with the energy the GPU drew per update where NVML is available (the
+    paper's closing conjecture, Sec. 7: fewer off-chip accesses may save energy)."""
     import torch
     out = {}
+    dev = torch.cuda.current_device()
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+        pci = "%08X:%02X:%02X.0" % (torch.cuda.get_device_properties(dev).pci_domain_id, bus,
+                                     torch.cuda.get_device_properties(dev).pci_device_id)
+    except Exception:
+        pci = None
+    meter = EnergyMeter(dev, pci)
     slt_prm = pcot.tile_params(tile=BEST_SLT["tile"], time_depth=BEST_SLT["time_depth"],
                                cot_threshold=BEST_SLT["cot_threshold"])
     cot_prm = pcot.tile_params(tile=BEST["tile"], time_depth=BEST["time_depth"], cot_threshold=BEST["cot_threshold"])
@@ -443,6 +514,9 @@ def compare_schedules(pcot, h, base, sizes, strides, stream):
             raise pcot.PcotError(st, name)
         ms = e0.elapsed_time(e1) / 3
         out[name] = {"ms": ms, "GUpdates/s": N_SIDE * N_SIDE * T_STEPS / ms / 1e6}
+        en = energy_per_update_nj(meter, run, torch.cuda.synchronize, N_SIDE * N_SIDE * T_STEPS)
+        if en is not None:
+            out[name]["energy"] = en
         if p is not None:
             out[name]["params"] = {"tile": list(p.tile)[:2], "time_depth": p.time_depth,
                                    "cot_threshold": list(p.cot_threshold)[:3]}

@@ -1,4 +1,5 @@
-"""The benchmark's multi-rank host logic on CPU: two gloo ranks.
+"""The benchmark's host logic on CPU: the multi-rank timing (two gloo ranks)
+and the energy accounting (against a fake NVML).
 
 The method has no exchange step between GPUs (each rank advances its own
 replica of the grid), so the only cross-rank operations are the barrier and
@@ -78,3 +79,54 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+class _FakeNVML:
+    """Stands in for libnvidia-ml: an energy counter that grows by 10 mJ per run."""
+
+    def __init__(self):
+        self.mj = 5_000
+        self.bus = None
+
+    def nvmlInit_v2(self):
+        return 0
+
+    def nvmlDeviceGetHandleByPciBusId_v2(self, bus, ref):
+        self.bus = bus
+        return 0
+
+    def nvmlDeviceGetHandleByIndex_v2(self, idx, ref):
+        return 0
+
+    def nvmlDeviceGetTotalEnergyConsumption(self, h, ref):
+        ref._obj.value = self.mj
+        return 0
+
+
+def test_energy_per_update_with_fake_nvml():
+    """Energy accounting of the schedule comparison: (counter delta) / (runs x
+    updates), here 10 mJ per run of 1e6 updates = 10 nJ per update."""
+    import time
+    import bench
+    fake = _FakeNVML()
+    meter = bench.EnergyMeter(0, "00000000:1B:00.0", lib=fake)
+    assert meter.ok and fake.bus == b"00000000:1B:00.0"
+
+    def run():
+        time.sleep(0.002)
+        fake.mj += 10
+
+    en = bench.energy_per_update_nj(meter, run, lambda: None, 1e6, min_seconds=0.02)
+    assert abs(en["nJ_per_update"] - 10.0) < 1e-9
+    assert en["runs"] >= 2 and en["avg_W"] > 0
+
+
+def test_energy_meter_absent_library_is_reported_not_raised():
+    import bench
+
+    class Broken:
+        def nvmlInit_v2(self):
+            return 9   # NVML_ERROR_DRIVER_NOT_LOADED-like failure
+
+    assert not bench.EnergyMeter(0, None, lib=Broken()).ok
+    assert bench.energy_per_update_nj(None, lambda: None, lambda: None, 1.0) is None
