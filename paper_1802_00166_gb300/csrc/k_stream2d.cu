@@ -35,7 +35,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxWarps = 8;
 constexpr int kRingSlots = 4;   // S
-constexpr int kRingRows = 4;    // G
+constexpr int kRingRows = 3;    // G: one fill per cycle of the 3-phase register ring
 
 template <int K, int E>
 struct Shape {
@@ -115,6 +115,9 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     const bool contiguous = !per || (col0 + (E - 1) < nx);
     const bool lvec = A.vec_ok && all_in && contiguous && (col0 % E) == 0;
     const bool svec = A.vec_ok && all_st && (xl % E) == 0;
+    bool any_st = false;
+#pragma unroll
+    for (int j = 0; j < E; ++j) any_st = any_st || st[j];
 
     const int64_t ybeg = y0 - K, yend = y0 + H + K;
     const int nrows = (int)(H + 2 * K);
@@ -218,27 +221,16 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     T* const dst_row0 = A.dst + xl + (y0 - 2 * K) * P;  // row of step 0 (only dereferenced in the store range)
     const int lane_ring = TMA ? box * A.box_elems + cc : 0;
 
-    auto step = [&](auto Uc, int i) {
+    // The K stages of step i (phase U of the register ring): level s+1 of row
+    // ybeg+i-s-1 from the three rows of level s, into out[] (level K).
+    struct Row {
+        T v[E];
+    };
+    auto stages = [&](auto Uc, int i) -> Row {
         constexpr int U = decltype(Uc)::value;
         constexpr int SA = U % 3, SB = (U + 1) % 3, SN = (U + 2) % 3;
-        if constexpr (TMA) {
-            const int f = i >> 2, r = i & (kRingRows - 1);
-            const uint32_t gi = fill_base + (uint32_t)f;
-            const int slot = (int)(gi & (kRingSlots - 1));
-            if (r == 0) {
-                if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
-                mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
-            }
-            const V q = *reinterpret_cast<const V*>(ring + (lane_ring + slot * A.slot_elems + r * A.BW));
-            const T* qq = reinterpret_cast<const T*>(&q);
-#pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
-        } else {
-#pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = pf[U][j];
-            if (i + 3 < nrows) load_row(ybeg + i + 3, pf[U]);
-        }
-        T out[E];
+        Row res;
+        T* out = res.v;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if constexpr (PK) {
@@ -287,27 +279,56 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 for (int j = 0; j < E; ++j) R[s + 1][SN][j] = out[j];
             }
         }
-        if constexpr (TMA) {
-            const int r = i & (kRingRows - 1);
-            if (r == kRingRows - 1 || i == nrows - 1) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[(fill_base + (uint32_t)(i >> 2)) & (kRingSlots - 1)]);
-            }
-        }
+        return res;
+    };
+
+    auto store = [&](int i, T* rowp, const Row& res) {
+        const T* out = res.v;
         if (i >= ist_lo && i < ist_hi) {
-            T* rowp = dst_row0 + (int64_t)i * P;
             if (svec) {
                 V q;
                 T* qq = reinterpret_cast<T*>(&q);
 #pragma unroll
                 for (int j = 0; j < E; ++j) qq[j] = out[slot_of<PK>(j)];
                 *reinterpret_cast<V*>(rowp) = q;
-            } else {
+            } else if (any_st) {
 #pragma unroll
                 for (int j = 0; j < E; ++j)
                     if (st[j]) rowp[j] = out[slot_of<PK>(j)];
             }
         }
+    };
+
+    // One step of the general loop (boundary warps, plain-load input).
+    auto step = [&](auto Uc, int i) {
+        constexpr int U = decltype(Uc)::value;
+        constexpr int SN = (U + 2) % 3;
+        if constexpr (TMA) {
+            const int f = i / kRingRows, r = i - f * kRingRows;
+            const uint32_t gi = fill_base + (uint32_t)f;
+            const int slot = (int)(gi & (kRingSlots - 1));
+            if (r == 0) {
+                if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
+                mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
+            }
+            const V q = *reinterpret_cast<const V*>(ring + (lane_ring + slot * A.slot_elems + r * A.BW));
+            const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = pf[U][j];
+            if (i + 3 < nrows) load_row(ybeg + i + 3, pf[U]);
+        }
+        const Row out = stages(Uc, i);
+        if constexpr (TMA) {
+            const int f = i / kRingRows;
+            if (i - f * kRingRows == kRingRows - 1 || i == nrows - 1) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(fill_base + (uint32_t)f) & (kRingSlots - 1)]);
+            }
+        }
+        store(i, dst_row0 + (int64_t)i * P, out);
     };
 
     if constexpr (CHECK) {
@@ -331,6 +352,36 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                     pf[2][j] = t0;
                 }
             }
+        }
+    } else if constexpr (TMA) {
+        // Interior warps fed by TMA: one ring fill of kRingRows = 3 rows per
+        // iteration, so the fill's wait and release and the phases of the
+        // register ring are fixed at compile time.  The last fill's rows past
+        // H + 2K are computed from real or zero-filled rows and never stored.
+        static_assert(kRingRows == 3, "one fill per cycle of the register ring");
+        auto fstep = [&](auto Uc, int ii, const T* src_row, T* out_row) {
+            constexpr int SN = (decltype(Uc)::value + 2) % 3;
+            const V q = *reinterpret_cast<const V*>(src_row);
+            const T* qq = reinterpret_cast<const T*>(&q);
+#pragma unroll
+            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
+            store(ii, out_row, stages(Uc, ii));
+        };
+        T* orow = dst_row0;
+        const T* const lane_base = ring + lane_ring;
+        for (int f = 0; f < nfill; ++f) {
+            const uint32_t gi = fill_base + (uint32_t)f;
+            const int slot = (int)(gi & (kRingSlots - 1));
+            if (producer && f + kRingSlots - 1 < nfill) issue(f + kRingSlots - 1);
+            mbar_wait(&full[slot], (gi / kRingSlots) & 1, A.st, A.timeout_ns, 2);
+            const T* srow = lane_base + slot * A.slot_elems;
+            const int i = 3 * f;
+            fstep(IC<0>{}, i, srow, orow);
+            fstep(IC<1>{}, i + 1, srow + A.BW, orow + P);
+            fstep(IC<2>{}, i + 2, srow + 2 * A.BW, orow + 2 * P);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            orow += 3 * P;
         }
     } else {
         for (int i = 0; i < nrows; i += 3) {
