@@ -35,9 +35,9 @@ HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
 METRIC = "GUpdates/s & DRAM bytes/update vs plain sweep; % HBM roofline at stated error"
 UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
-BEST = {"schedule": "cot", "tile": (80, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
+BEST = {"schedule": "cot", "tile": (80, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
 BEST_SLT = {"schedule": "slt", "tile": (40, 112), "time_depth": 4, "cot_threshold": (2, 256, 256)}
-BATCH = {"tile": (96, 112), "time_depth": 4, "cot_threshold": (2, 256, 256)}
+BATCH = {"tile": (96, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 

@@ -20,9 +20,9 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 THREADS = os.cpu_count() or 1
 # The benchmark's timed configuration (bench.py BEST): recursive-order
-# persistent executor, tiles of depth 6, 80 rows x one warp, leaf orthants of
+# persistent executor, tiles of depth 8, 80 rows x one warp, leaf orthants of
 # 2 blocks x 256 x 256 tiles, rows padded to 128 bytes.
-BENCH_PARAMS = dict(tile=(80, 112), time_depth=6, cot_threshold=(2, 256, 256))
+BENCH_PARAMS = dict(tile=(80, 112), time_depth=8, cot_threshold=(2, 256, 256))
 
 
 @pytest.fixture(scope="module", autouse=True)
