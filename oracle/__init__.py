@@ -16,6 +16,10 @@ Contents
   * ``grid_sum``     correctly rounded sum of the interior (math.fsum).
   * ``mlp``          FP64 MLP forward/backward/Adam (module ``oracle.mlp``).
   * ``legality``     tile-level hazard checker for tile queues (``oracle.legality``).
+  * ``gs2d`` / ``gs2d_pcot`` / ``gs2d_box_empty`` / ``gs2d_tile_order``
+                     Gauss-Seidel 2-D (in place, 9-point average): the plain
+                     loop nest and the recursive order over its skewed space
+                     (C, ``oracle_gs.c``).
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "oracle_gs.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -40,10 +45,10 @@ _I32P = ctypes.POINTER(ctypes.c_int32)
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` with plain IEEE binary64 semantics."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC]
+           "-shared", "-fPIC", "-o", _LIB + ".tmp"] + _SRCS
     subprocess.run(cmd, check=True)
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -67,6 +72,16 @@ def _load():
             lib.oracle_orthant_empty.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64,
                                                  _I64P, _I64P]
             lib.oracle_orthant_empty.restype = ctypes.c_int
+            lib.oracle_gs2d.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _F64P, ctypes.c_int64]
+            lib.oracle_gs2d.restype = ctypes.c_int
+            lib.oracle_gs2d_pcot.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _F64P, ctypes.c_int64,
+                                             _I64P, _I64P]
+            lib.oracle_gs2d_pcot.restype = ctypes.c_int
+            lib.oracle_gs2d_box_empty.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P, _I64P]
+            lib.oracle_gs2d_box_empty.restype = ctypes.c_int
+            lib.oracle_gs2d_tile_order.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P, _I64P,
+                                                   _I64P, ctypes.c_int64]
+            lib.oracle_gs2d_tile_order.restype = ctypes.c_int64
             lib.oracle_pcot_order.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64, _I64P,
                                               _I64P, ctypes.c_int64]
             lib.oracle_pcot_order.restype = ctypes.c_int64
@@ -172,6 +187,50 @@ def orthant_empty(sizes, T, lo, size, radius=1):
     if rc < 0:
         raise RuntimeError("oracle_orthant_empty failed")
     return rc
+
+
+# ---- Gauss-Seidel 2-D (oracle_gs.c) -------------------------------------
+
+def gs2d(grid, T):
+    """T in-place lexicographic Gauss-Seidel steps of the 9-point average on a
+    (n0+2) x (n1+2) FP64 grid with a fixed ring; returns a new array."""
+    u = np.ascontiguousarray(np.array(grid, dtype=np.float64))
+    n0, n1 = u.shape[0] - 2, u.shape[1] - 2
+    if _load().oracle_gs2d(n0, n1, u.shape[1], _ptr(u, _F64P), int(T)) != 0:
+        raise ValueError("oracle_gs2d: bad arguments")
+    return u
+
+
+def gs2d_pcot(grid, T, leaf, return_stats=False):
+    """The same steps in the paper's recursive order over the skewed space
+    (t, t+i, 2t+i+j) with leaf box `leaf` (three widths)."""
+    u = np.ascontiguousarray(np.array(grid, dtype=np.float64))
+    n0, n1 = u.shape[0] - 2, u.shape[1] - 2
+    lf = _i64(leaf)
+    st = np.zeros(4, dtype=np.int64)
+    if _load().oracle_gs2d_pcot(n0, n1, u.shape[1], _ptr(u, _F64P), int(T), _ptr(lf, _I64P), _ptr(st, _I64P)) != 0:
+        raise ValueError("oracle_gs2d_pcot: bad arguments")
+    if return_stats:
+        return u, dict(leaves=int(st[0]), zero_exits=int(st[1]), empty_exits=int(st[2]), points=int(st[3]))
+    return u
+
+
+def gs2d_box_empty(n0, n1, T, lo, hi):
+    """Exact emptiness of an inclusive box of skewed points (t, a, c)."""
+    return bool(_load().oracle_gs2d_box_empty(int(n0), int(n1), int(T), _ptr(_i64(lo), _I64P), _ptr(_i64(hi), _I64P)))
+
+
+def gs2d_tile_order(n0, n1, T, tile, theta):
+    """Non-empty tiles (b0, b1, b2) of the skewed lattice in the recursive
+    order, as an (count, 3) int64 array."""
+    lib = _load()
+    tl, th = _i64(tile), _i64(theta)
+    n = lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), None, 0)
+    if n < 0:
+        raise ValueError("oracle_gs2d_tile_order: bad arguments")
+    out = np.zeros((max(n, 1), 3), dtype=np.int64)
+    lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), _ptr(out, _I64P), n)
+    return out[:n]
 
 
 def interior(grid, sizes, radius=1, periodic=False):
