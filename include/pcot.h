@@ -353,6 +353,53 @@ pcot_status pcot_run_noalloc(pcot_handle h, void *grid, const int64_t *sizes, co
                              int64_t T, pcot_dtype dtype, pcot_schedule schedule,
                              const pcot_tile_params *params, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Gauss-Seidel 2-D (GS-2D, one of the stencils of the paper's benchmark
+ * suite, Sec. 5.1.2): T in-place steps over an (n0 + 2) x (n1 + 2) grid
+ * with a fixed ring; one step visits the interior rows i = 1..n0 and, within
+ * a row, the columns j = 1..n1 in increasing order and sets
+ *   u[i][j] = (u[i-1][j-1] + u[i-1][j] + u[i-1][j+1] + u[i][j-1] + u[i][j]
+ *              + u[i][j+1] + u[i+1][j-1] + u[i+1][j] + u[i+1][j+1]) / 9
+ * (adds left to right, each rounded; one rounded division), so the north row
+ * and the west neighbour are already this step's values.  The GPU runs tiles
+ * of the skewed space (t, t + i, 2t + i + j) (Sec. 4.1), in which every
+ * dependence has non-negative components, with a persistent executor:
+ *   PCOT_SWEEP  tiles one step deep (time_depth 1), wavefront order;
+ *   PCOT_SLT    tiles time_depth steps deep, wavefront order (tiles with
+ *               equal b0 + b1 + b2 are independent and run together);
+ *   PCOT_COT    the recursive order of Sec. 4.2-4.3 over the tile lattice
+ *               (orthants with equal numbers of upper halves side by side).
+ * Every dtype evaluates the definition's operations in its order: PCOT_F64
+ * and PCOT_F64_EXACT are bitwise equal to the plain loop nest in binary64;
+ * PCOT_F32 rounds each operation to binary32.
+ *
+ * sizes: {n0, n1} interior rows and columns.  strides: {row stride, 1} or
+ * NULL (row stride n1 + 2).  params: tile = {ha, wc} skewed rows and
+ * columns per tile (default 32, 128; ha * time_depth <= 1024 threads, wc >= 2),
+ * time_depth = kt (default 1 for PCOT_SWEEP, else 8), cot_threshold[0..2] =
+ * recursion leaf in tiles along (t, a, c) (default 2, 4, 4).  The handle
+ * supplies the device status block (its coefficients are not used).  The
+ * workspace (device, 256-byte aligned, pcot_gs2d_workspace_bytes) holds the
+ * tile queue and dependency counters.  Asynchronous on `stream`; a
+ * dependency wait that times out is reported by pcot_check.
+ * ------------------------------------------------------------------------ */
+pcot_status pcot_gs2d_workspace_bytes(const int64_t *sizes, int64_t T, pcot_schedule schedule,
+                                      const pcot_tile_params *params, size_t *bytes);
+pcot_status pcot_gs2d_run(pcot_handle h, void *grid, void *workspace, size_t workspace_bytes,
+                          const int64_t *sizes, const int64_t *strides, int64_t T, pcot_dtype dtype,
+                          pcot_schedule schedule, const pcot_tile_params *params, void *stream);
+/*
+ * The GS-2D tile plan without running it (host only, no GPU needed):
+ * lattice[3] tiles along (t, a, c), tile[3] = {kt, ha, wc}, *n_tiles the
+ * number of non-empty tiles; queue (n_tiles entries, linear ids
+ * (b0 * L1 + b1) * L2 + b2 in execution order) and deps (L0 * L1 * L2
+ * entries: predecessors of each id among its seven lower neighbours that hold
+ * points) are filled up to cap entries when not NULL.
+ */
+pcot_status pcot_gs2d_plan_query(const int64_t *sizes, int64_t T, pcot_schedule schedule,
+                                 const pcot_tile_params *params, int32_t *lattice, int32_t *tile,
+                                 int64_t *n_tiles, int32_t *queue, int32_t *deps, int64_t cap);
+
 /*
  * Number of kernels this handle has launched since it was created (sweep
  * steps, single-level blocks, persistent executors, ring copies, sums).

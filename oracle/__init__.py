@@ -80,7 +80,7 @@ def _load():
             lib.oracle_gs2d_box_empty.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P, _I64P]
             lib.oracle_gs2d_box_empty.restype = ctypes.c_int
             lib.oracle_gs2d_tile_order.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P, _I64P,
-                                                   _I64P, ctypes.c_int64]
+                                                   ctypes.c_int, _I64P, ctypes.c_int64]
             lib.oracle_gs2d_tile_order.restype = ctypes.c_int64
             lib.oracle_pcot_order.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64, _I64P,
                                               _I64P, ctypes.c_int64]
@@ -220,16 +220,18 @@ def gs2d_box_empty(n0, n1, T, lo, hi):
     return bool(_load().oracle_gs2d_box_empty(int(n0), int(n1), int(T), _ptr(_i64(lo), _I64P), _ptr(_i64(hi), _I64P)))
 
 
-def gs2d_tile_order(n0, n1, T, tile, theta):
+def gs2d_tile_order(n0, n1, T, tile, theta, wavefront=False):
     """Non-empty tiles (b0, b1, b2) of the skewed lattice in the recursive
-    order, as an (count, 3) int64 array."""
+    order (children and leaves lexicographic, or grouped into wavefronts), as
+    an (count, 3) int64 array."""
     lib = _load()
     tl, th = _i64(tile), _i64(theta)
-    n = lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), None, 0)
+    wf = 1 if wavefront else 0
+    n = lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), wf, None, 0)
     if n < 0:
         raise ValueError("oracle_gs2d_tile_order: bad arguments")
     out = np.zeros((max(n, 1), 3), dtype=np.int64)
-    lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), _ptr(out, _I64P), n)
+    lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), wf, _ptr(out, _I64P), n)
     return out[:n]
 
 

@@ -210,13 +210,25 @@ int oracle_gs2d_pcot(int64_t n0, int64_t n1, int64_t s0, double *u, int64_t T, c
  * lattice's bounding box [0, L0) x [0, L1) x [0, L2) is padded to
  * theta_d * 2^k_d tiles, split into orthants as above (zero and empty exits,
  * a box of tiles being empty when the points it covers are), and a leaf box
- * lists its non-empty tiles lexicographically.  Records (b0, b1, b2) of each
+ * lists its non-empty tiles lexicographically.  With `wavefront` set, the
+ * children of a box are visited grouped by their number of upper halves
+ * (orthants with equal counts are independent: the wavefronts of the
+ * parallel recursion) and a leaf lists its tiles by b0 + b1 + b2, then
+ * lexicographically -- the order a GPU executor uses to expose parallelism.  Records (b0, b1, b2) of each
  * non-empty tile in order, up to cap; returns their number. */
 typedef struct {
     int64_t n0, n1, T, tile[3], theta[3];
     int64_t *out;
     int64_t cap, count;
+    int wavefront;  /* children by number of upper halves, leaves by b0+b1+b2 */
 } gs_tiles;
+
+static void gs_tiles_emit(gs_tiles *q, const int64_t *b)
+{
+    if (q->out && q->count < q->cap)
+        for (int d = 0; d < 3; ++d) q->out[3 * q->count + d] = b[d];
+    ++q->count;
+}
 
 static int gs_tiles_empty(const gs_tiles *q, const int64_t *blo, const int64_t *bhi)
 {
@@ -241,14 +253,20 @@ static void gs_tiles_recurse(gs_tiles *q, const int64_t *lo, const int64_t *size
         if (size[d] > q->theta[d]) base = 0;
     if (base) {
         int64_t b[3];
-        for (b[0] = lo[0]; b[0] <= hi[0]; ++b[0])
-            for (b[1] = lo[1]; b[1] <= hi[1]; ++b[1])
-                for (b[2] = lo[2]; b[2] <= hi[2]; ++b[2]) {
-                    if (gs_tiles_empty(q, b, b)) continue;
-                    if (q->out && q->count < q->cap)
-                        for (int d = 0; d < 3; ++d) q->out[3 * q->count + d] = b[d];
-                    ++q->count;
-                }
+        if (q->wavefront) {
+            for (int64_t w = lo[0] + lo[1] + lo[2]; w <= hi[0] + hi[1] + hi[2]; ++w)
+                for (b[0] = lo[0]; b[0] <= hi[0]; ++b[0])
+                    for (b[1] = lo[1]; b[1] <= hi[1]; ++b[1]) {
+                        b[2] = w - b[0] - b[1];
+                        if (b[2] < lo[2] || b[2] > hi[2] || gs_tiles_empty(q, b, b)) continue;
+                        gs_tiles_emit(q, b);
+                    }
+        } else {
+            for (b[0] = lo[0]; b[0] <= hi[0]; ++b[0])
+                for (b[1] = lo[1]; b[1] <= hi[1]; ++b[1])
+                    for (b[2] = lo[2]; b[2] <= hi[2]; ++b[2])
+                        if (!gs_tiles_empty(q, b, b)) gs_tiles_emit(q, b);
+        }
         return;
     }
     int64_t half[3][2];
@@ -261,24 +279,28 @@ static void gs_tiles_recurse(gs_tiles *q, const int64_t *lo, const int64_t *size
             half[d][1] = 0;
         }
     }
-    for (int m = 0; m < 8; ++m) {
-        int64_t clo[3], csz[3];
-        for (int d = 0; d < 3; ++d) {
-            const int bit = (m >> (2 - d)) & 1;
-            clo[d] = lo[d] + (bit ? half[d][0] : 0);
-            csz[d] = half[d][bit];
+    /* lexicographic children, or grouped by their number of upper halves */
+    for (int pass = 0; pass < (q->wavefront ? 4 : 1); ++pass)
+        for (int m = 0; m < 8; ++m) {
+            const int ups = ((m >> 2) & 1) + ((m >> 1) & 1) + (m & 1);
+            if (q->wavefront && ups != pass) continue;
+            int64_t clo[3], csz[3];
+            for (int d = 0; d < 3; ++d) {
+                const int bit = (m >> (2 - d)) & 1;
+                clo[d] = lo[d] + (bit ? half[d][0] : 0);
+                csz[d] = half[d][bit];
+            }
+            gs_tiles_recurse(q, clo, csz);
         }
-        gs_tiles_recurse(q, clo, csz);
-    }
 }
 
 int64_t oracle_gs2d_tile_order(int64_t n0, int64_t n1, int64_t T, const int64_t *tile, const int64_t *theta,
-                               int64_t *out, int64_t cap)
+                               int wavefront, int64_t *out, int64_t cap)
 {
     if (n0 < 1 || n1 < 1 || T < 0 || !tile || !theta) return -1;
     for (int d = 0; d < 3; ++d)
         if (tile[d] < 1 || theta[d] < 1) return -1;
-    gs_tiles q = {n0, n1, T, {tile[0], tile[1], tile[2]}, {theta[0], theta[1], theta[2]}, out, cap, 0};
+    gs_tiles q = {n0, n1, T, {tile[0], tile[1], tile[2]}, {theta[0], theta[1], theta[2]}, out, cap, 0, wavefront};
     if (T == 0) return 0;
     const int64_t ext[3] = {T, T - 1 + n0, 2 * T - 3 + n0 + n1};
     int64_t lo[3] = {0, 0, 0}, size[3];

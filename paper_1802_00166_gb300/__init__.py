@@ -116,6 +116,12 @@ def _load():
                               ctypes.POINTER(ctypes.c_float)]),
         "pcot_run_noalloc": (S, [_VP, _VP, _I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_gs2d_workspace_bytes": (S, [_I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_gs2d_run": (S, [_VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64, ctypes.c_int,
+                              ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_gs2d_plan_query": (S, [_I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _I32P,
+                                     _I32P, _I64P, _I32P, _I32P, ctypes.c_int64]),
         "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
@@ -130,7 +136,8 @@ def _load():
 
 def exported_symbols():
     """Names declared in include/pcot.h that this binding marshals."""
-    return ["pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
+    return ["pcot_gs2d_workspace_bytes", "pcot_gs2d_run", "pcot_gs2d_plan_query",
+            "pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
             "pcot_run_host", "pcot_check", "pcot_plan_query", "pcot_test_wait_timeout", "pcot_grid_sum",
             "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
             "pcot_batch_destroy", "pcot_run_batched", "pcot_autotune", "pcot_mlp_param_count",
@@ -224,6 +231,41 @@ def pcot_run_noalloc(h, grid, sizes, strides, T, dtype, schedule, params=None, s
     s, st = _i64(sizes), _i64(strides)
     _chk(_load().pcot_run_noalloc(h, _ptr(grid), _p64(s), _p64(st), int(T), int(dtype), int(schedule),
                                   _params(params), _stream(stream)), "pcot_run_noalloc")
+
+
+def pcot_gs2d_workspace_bytes(sizes, T, schedule, params=None):
+    n = ctypes.c_size_t()
+    _chk(_load().pcot_gs2d_workspace_bytes(_p64(_i64(sizes)), int(T), int(schedule), _params(params),
+                                           ctypes.byref(n)), "pcot_gs2d_workspace_bytes")
+    return n.value
+
+
+def pcot_gs2d_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule, params=None, stream=None):
+    """Gauss-Seidel 2-D, in place on a device grid (see include/pcot.h)."""
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_gs2d_run(h, _ptr(grid), _ptr(workspace), int(workspace_bytes), _p64(s), _p64(st), int(T),
+                               int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_gs2d_run")
+
+
+def pcot_gs2d_plan_query(sizes, T, schedule, params=None, with_queue=True):
+    lib = _load()
+    s = _i64(sizes)
+    lat = (ctypes.c_int32 * 3)()
+    tl = (ctypes.c_int32 * 3)()
+    nt = ctypes.c_int64()
+    _chk(lib.pcot_gs2d_plan_query(_p64(s), int(T), int(schedule), _params(params), lat, tl, ctypes.byref(nt),
+                                  None, None, 0), "pcot_gs2d_plan_query")
+    out = dict(lattice=list(lat), tile=list(tl), n_tiles=nt.value)
+    if with_queue:
+        ncell = lat[0] * lat[1] * lat[2]
+        cap = max(nt.value, ncell)
+        qq = np.zeros(cap, dtype=np.int32)
+        dd = np.zeros(cap, dtype=np.int32)
+        _chk(lib.pcot_gs2d_plan_query(_p64(s), int(T), int(schedule), _params(params), None, None, None,
+                                      qq.ctypes.data_as(_I32P), dd.ctypes.data_as(_I32P), cap), "pcot_gs2d_plan_query")
+        out["queue"] = qq[:nt.value].copy()
+        out["deps"] = dd[:ncell].copy()
+    return out
 
 
 def pcot_run_host(h, host_grid, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,

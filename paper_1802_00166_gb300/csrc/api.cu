@@ -35,6 +35,14 @@ struct CotPlanHost {
     size_t image_bytes = 0;
 };
 
+// Gauss-Seidel 2-D plan with its upload image ([head block][counts][queue]).
+struct GsPlanCache {
+    GsPlanHost plan;
+    int32_t tile[3] = {0, 0, 0};
+    void* pinned = nullptr;
+    size_t image_bytes = 0, counts_bytes = 0;
+};
+
 }  // namespace
 
 struct pcot_plan {
@@ -46,6 +54,7 @@ struct pcot_plan {
     DevStatus* d_status = nullptr;
     double* d_partials = nullptr;  // grid-sum partials
     std::map<std::string, CotPlanHost*> cot_cache;
+    std::map<std::string, GsPlanCache*> gs_cache;
     uint64_t timeout_ns = kDefaultTimeoutNs;
     int64_t launches = 0;  // kernels launched by this handle
 };
@@ -376,6 +385,10 @@ pcot_status pcot_create(int dims, int radius, const double* coeffs, int ncoeffs,
 pcot_status pcot_destroy(pcot_handle h) {
     if (!h) return PCOT_ERR_INVALID_ARG;
     for (auto& kv : h->cot_cache) {
+        if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+        delete kv.second;
+    }
+    for (auto& kv : h->gs_cache) {
         if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
         delete kv.second;
     }
@@ -982,3 +995,175 @@ void handle_count_launches(pcot_handle h, int64_t n) {
     if (h) h->launches += n;
 }
 }  // namespace pcot
+
+// ---- Gauss-Seidel 2-D ---------------------------------------------------
+namespace {
+
+// Tile shape and recursion threshold of a GS-2D run (defaults per schedule).
+bool gs_shape(pcot_schedule schedule, const pcot_tile_params* p, int32_t* tile, int32_t* theta) {
+    if (schedule != PCOT_SWEEP && schedule != PCOT_SLT && schedule != PCOT_COT) return false;
+    const int kt_def = schedule == PCOT_SWEEP ? 1 : 8;
+    tile[0] = (p && p->time_depth > 0) ? p->time_depth : kt_def;
+    tile[1] = (p && p->tile[0] > 0) ? p->tile[0] : 32;
+    tile[2] = (p && p->tile[1] > 0) ? p->tile[1] : 128;
+    if (schedule == PCOT_SWEEP && tile[0] != 1) return false;
+    for (int d = 0; d < 3; ++d) theta[d] = (p && p->cot_threshold[d] > 0) ? p->cot_threshold[d] : (d == 0 ? 2 : 4);
+    if (tile[0] * tile[1] > 1024 || tile[0] * tile[1] < 1 || tile[2] < 2 || tile[2] > 4096) return false;
+    return true;
+}
+
+pcot_status gs_get_plan(pcot_handle h, int64_t n0, int64_t n1, int64_t T, pcot_schedule schedule,
+                        const int32_t* tile, const int32_t* theta, GsPlanCache** out) {
+    char key[160];
+    snprintf(key, sizeof(key), "%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%d", (long long)n0, (long long)n1, (long long)T,
+             (int)schedule, tile[0], tile[1], tile[2], theta[0], theta[1], theta[2]);
+    if (h) {
+        auto it = h->gs_cache.find(key);
+        if (it != h->gs_cache.end()) {
+            *out = it->second;
+            return PCOT_OK;
+        }
+    }
+    GsPlanCache* c = new GsPlanCache();
+    if (!gs_plan(n0, n1, T, tile, schedule == PCOT_COT ? 1 : 0, theta, &c->plan)) {
+        delete c;
+        return PCOT_ERR_UNSUPPORTED;
+    }
+    for (int d = 0; d < 3; ++d) c->tile[d] = tile[d];
+    c->counts_bytes = round_up(c->plan.deps.size() * 4, kAlign);
+    c->image_bytes = kAlign + c->counts_bytes + round_up(c->plan.queue.size() * 4 + 4, kAlign);
+    if (h) {
+        if (h->gs_cache.size() >= 16) {
+            for (auto& kv : h->gs_cache) {
+                if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+                delete kv.second;
+            }
+            h->gs_cache.clear();
+        }
+        h->gs_cache[key] = c;
+    }
+    *out = c;
+    return PCOT_OK;
+}
+
+pcot_status gs_check_args(const int64_t* sizes, const int64_t* strides, int64_t T, int64_t* pitch) {
+    if (!sizes || T < 0) return PCOT_ERR_INVALID_ARG;
+    if (sizes[0] < 1 || sizes[1] < 1 || sizes[0] > (1LL << 30) || sizes[1] > (1LL << 30)) return PCOT_ERR_INVALID_ARG;
+    if (strides) {
+        if (strides[1] != 1) return PCOT_ERR_UNSUPPORTED;
+        if (strides[0] < sizes[1] + 2) return PCOT_ERR_INVALID_ARG;
+        *pitch = strides[0];
+    } else {
+        *pitch = sizes[1] + 2;
+    }
+    return PCOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcot_status pcot_gs2d_plan_query(const int64_t* sizes, int64_t T, pcot_schedule schedule,
+                                 const pcot_tile_params* params, int32_t* lattice, int32_t* tile, int64_t* n_tiles,
+                                 int32_t* queue, int32_t* deps, int64_t cap) {
+    int64_t pitch = 0;
+    PCOT_TRY(gs_check_args(sizes, nullptr, T, &pitch));
+    if (T < 1) return PCOT_ERR_INVALID_ARG;
+    int32_t tl[3], th[3];
+    if (!gs_shape(schedule, params, tl, th)) return PCOT_ERR_UNSUPPORTED;
+    GsPlanCache* c = nullptr;
+    PCOT_TRY(gs_get_plan(nullptr, sizes[0], sizes[1], T, schedule, tl, th, &c));
+    for (int d = 0; d < 3; ++d) {
+        if (lattice) lattice[d] = c->plan.lattice[d];
+        if (tile) tile[d] = tl[d];
+    }
+    if (n_tiles) *n_tiles = (int64_t)c->plan.queue.size();
+    if (queue)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.queue.size(); ++k) queue[k] = c->plan.queue[(size_t)k];
+    if (deps)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.deps.size(); ++k) deps[k] = c->plan.deps[(size_t)k];
+    delete c;
+    return PCOT_OK;
+}
+
+pcot_status pcot_gs2d_workspace_bytes(const int64_t* sizes, int64_t T, pcot_schedule schedule,
+                                      const pcot_tile_params* params, size_t* bytes) {
+    if (!bytes) return PCOT_ERR_INVALID_ARG;
+    int64_t pitch = 0;
+    PCOT_TRY(gs_check_args(sizes, nullptr, T, &pitch));
+    int32_t tl[3], th[3];
+    if (!gs_shape(schedule, params, tl, th)) return PCOT_ERR_UNSUPPORTED;
+    if (T == 0) {
+        *bytes = 0;
+        return PCOT_OK;
+    }
+    int64_t L[3];
+    const int64_t ext[3] = {T, T - 1 + sizes[0], 2 * T - 3 + sizes[0] + sizes[1]};
+    for (int d = 0; d < 3; ++d) L[d] = (ext[d] + tl[d] - 1) / tl[d];
+    const int64_t cells = L[0] * L[1] * L[2];
+    if (cells > (1LL << 28)) return PCOT_ERR_UNSUPPORTED;
+    // head block + counts of every lattice id + the queue (at most every id)
+    *bytes = kAlign + round_up((size_t)cells * 4, kAlign) + round_up((size_t)cells * 4 + 4, kAlign);
+    return PCOT_OK;
+}
+
+pcot_status pcot_gs2d_run(pcot_handle h, void* grid, void* workspace, size_t workspace_bytes, const int64_t* sizes,
+                          const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
+                          const pcot_tile_params* params, void* stream) {
+    if (!h || !grid) return PCOT_ERR_INVALID_ARG;
+    if (dtype != PCOT_F32 && dtype != PCOT_F64 && dtype != PCOT_F64_EXACT) return PCOT_ERR_INVALID_ARG;
+    int64_t pitch = 0;
+    PCOT_TRY(gs_check_args(sizes, strides, T, &pitch));
+    int32_t tl[3], th[3];
+    if (!gs_shape(schedule, params, tl, th)) return PCOT_ERR_UNSUPPORTED;
+    if (((uintptr_t)grid % (dtype == PCOT_F32 ? 4 : 8)) != 0) return PCOT_ERR_ALIGNMENT;
+    if (T == 0) return PCOT_OK;
+    size_t need = 0;
+    PCOT_TRY(pcot_gs2d_workspace_bytes(sizes, T, schedule, params, &need));
+    if (!workspace || workspace_bytes < need) return PCOT_ERR_OOM;
+    if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
+    PCOT_TRY(ensure_device(h));
+    GsPlanCache* c = nullptr;
+    PCOT_TRY(gs_get_plan(h, sizes[0], sizes[1], T, schedule, tl, th, &c));
+    if (c->plan.queue.empty()) return PCOT_OK;
+    if (!c->pinned) {
+        void* p = nullptr;
+        PCOT_CUDA(cudaMallocHost(&p, c->image_bytes));
+        unsigned char* img = (unsigned char*)p;
+        std::memset(img, 0, c->image_bytes);
+        std::memcpy(img + kAlign, c->plan.deps.data(), c->plan.deps.size() * 4);
+        std::memcpy(img + kAlign + c->counts_bytes, c->plan.queue.data(), c->plan.queue.size() * 4);
+        c->pinned = p;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* ws = (unsigned char*)workspace;
+    PCOT_CUDA(cudaMemcpyAsync(ws, c->pinned, c->image_bytes, cudaMemcpyHostToDevice, s));
+    GsDev q;
+    std::memset(&q, 0, sizeof(q));
+    q.head = (int32_t*)ws;
+    q.counts = (int32_t*)(ws + kAlign);
+    q.queue = (const int32_t*)(ws + kAlign + c->counts_bytes);
+    q.ntiles = (int64_t)c->plan.queue.size();
+    for (int d = 0; d < 3; ++d) {
+        q.lattice[d] = c->plan.lattice[d];
+        q.tile[d] = tl[d];
+    }
+    q.n0 = sizes[0];
+    q.n1 = sizes[1];
+    q.T = T;
+    q.pitch = pitch;
+    gs2d_window(&q);
+    q.status = h->d_status;
+    q.timeout_ns = h->timeout_ns;
+    const int dt = dtype == PCOT_F32 ? kF32 : kF64;
+    if (gs2d_smem_bytes(dt, q) > 227 * 1024) return PCOT_ERR_UNSUPPORTED;
+    const int per_sm = gs2d_ctas_per_sm(dt, q);
+    if (per_sm < 1) return PCOT_ERR_UNSUPPORTED;
+    int64_t nctas = (int64_t)per_sm * h->num_sms;
+    if (nctas > q.ntiles) nctas = q.ntiles;
+    PCOT_CUDA(launch_gs2d(dt, grid, q, (int)nctas, s));
+    ++h->launches;
+    return PCOT_OK;
+}
+
+}  // extern "C"

@@ -42,6 +42,26 @@ struct CotDev {
     uint64_t timeout_ns;
 };
 
+// ---- k_gs2d.cu: Gauss-Seidel 2-D tiles over the skewed (t, t+i, 2t+i+j) space ----
+struct GsDev {
+    const int32_t* queue;  // non-empty tile ids in execution order
+    int32_t* counts;       // remaining predecessors per lattice id
+    int32_t* head;         // next queue position to pop
+    int64_t ntiles;
+    int32_t lattice[3];    // tiles along t, a = t+i, c = 2t+i+j
+    int32_t tile[3];       // kt, ha, wc (skewed points per tile)
+    int64_t n0, n1, T;     // interior rows, columns, time steps
+    int64_t pitch;         // row stride of the grid (elements)
+    int32_t rows, cols;    // shared-memory window of a tile (halo included; cols padded)
+    DevStatus* status;
+    uint64_t timeout_ns;
+};
+// Window geometry of a tile (rows, padded columns) and its shared-memory bytes.
+void gs2d_window(GsDev* q);
+size_t gs2d_smem_bytes(int dtype, const GsDev& q);
+int gs2d_ctas_per_sm(int dtype, const GsDev& q);
+cudaError_t launch_gs2d(int dtype, void* grid, const GsDev& q, int nctas, cudaStream_t s);
+
 // ---- k_sweep.cu ----
 cudaError_t launch_sweep(const LaunchCtx& L, const void* src, void* dst);
 cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst);

@@ -38,4 +38,17 @@ std::vector<int32_t> pcot_lattice_order(int P, int dims, const int64_t* L, const
 // previous block within lattice distance 1 (0 for the first block).
 std::vector<int32_t> lattice_dep_counts(int P, int dims, const int64_t* L);
 
+// Gauss-Seidel 2-D tile plan (planner_gs.cpp): lattice extents of the
+// skewed (t, t+i, 2t+i+j) space in tiles, the non-empty tiles' linear ids
+// (b0 * L1 + b1) * L2 + b2 in execution order (wavefront, or the recursive
+// order when `recursive`), and per lattice id the number of non-empty
+// predecessors among its seven lower neighbours.
+struct GsPlanHost {
+    int32_t lattice[3] = {0, 0, 0};
+    std::vector<int32_t> queue;
+    std::vector<int32_t> deps;
+};
+bool gs_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
+             GsPlanHost* out);
+
 }  // namespace pcot
