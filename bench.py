@@ -411,16 +411,63 @@ def run_gpu(args):
                                 "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
     if args.schedules and rank == 0:
         line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
-    if args.batched and rank == 0:
+    if (args.batched or args.gs2d) and rank == 0:
         del base, wsbuf, host
         torch.cuda.empty_cache()
+    if args.batched and rank == 0:
         line["batched"] = run_batched(pcot, stream, args.steps)
+    if args.gs2d and rank == 0:
+        line["gs2d"] = run_gs2d(pcot, h, stream, args.steps)
     pcot.pcot_destroy(h)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+GS2D = {"n": 2000, "T": 500, "slt": {"tile": (32, 128), "time_depth": 8},
+        "slt_f64": {"tile": (16, 128), "time_depth": 8},
+        "cot": {"tile": (32, 128), "time_depth": 8, "cot_threshold": (8, 16, 16)}}
+
+
+def run_gs2d(pcot, h, stream, steps):
+    """Gauss-Seidel 2-D at the paper's size (2000^2 interior, T = 500; Table 2):
+    in place on the device, sweep / single-level (wavefront) / recursive tile
+    orders, FP64 (bitwise the loop nest) and FP32; CUDA events, inputs resident."""
+    import torch
+    n, T = GS2D["n"], GS2D["T"]
+    out = {"workload": f"gs2d-9pt {n}x{n} T={T} in place", "unit": "GUpdates/s"}
+    for dtype, dn in ((pcot.PCOT_F64, "f64"), (pcot.PCOT_F32, "f32")):
+        tdt = torch.float32 if dtype == pcot.PCOT_F32 else torch.float64
+        base = torch.rand((n + 2) * (n + 2), dtype=tdt, device="cuda")
+        for name, sched, prm in (("sweep", pcot.PCOT_SWEEP, None),
+                                 ("slt", pcot.PCOT_SLT, GS2D["slt_f64" if dn == "f64" else "slt"]),
+                                 ("cot", pcot.PCOT_COT, GS2D["cot"])):
+            p = pcot.tile_params(**prm) if prm else None
+            nb = pcot.pcot_gs2d_workspace_bytes((n, n), T, sched, p)
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            run = lambda: pcot.pcot_gs2d_run(h, base.data_ptr(), ws.data_ptr(), nb, (n, n), None, T, dtype, sched,
+                                             p, stream)
+            for _ in range(2):
+                run()
+            torch.cuda.synchronize()
+            reps = max(1, min(steps, 3))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = pcot.pcot_check(h, stream)
+            if st != pcot.PCOT_OK:
+                raise pcot.PcotError(st, "gs2d " + name)
+            ms = e0.elapsed_time(e1) / reps
+            out[f"{name}_{dn}"] = {"ms": ms, "GUpdates/s": n * n * T / ms / 1e6,
+                                   "params": {k: list(v) if isinstance(v, tuple) else v for k, v in (prm or {}).items()}}
+        del base
+    return out
 
 
 def run_batched(pcot, stream, steps):
@@ -561,6 +608,7 @@ def main():
     ap.add_argument("--schedules", action="store_true", help="also time sweep / SLT / COT side by side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true", help="also time the 256-grid batched persistent launch")
+    ap.add_argument("--gs2d", action="store_true", help="also time Gauss-Seidel 2-D at the paper's size")
     ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
     ap.add_argument("--case-n", type=int, default=8192)
