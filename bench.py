@@ -464,7 +464,14 @@ def run_gs2d(pcot, h, stream, steps):
             if st != pcot.PCOT_OK:
                 raise pcot.PcotError(st, "gs2d " + name)
             ms = e0.elapsed_time(e1) / reps
-            out[f"{name}_{dn}"] = {"ms": ms, "GUpdates/s": n * n * T / ms / 1e6,
+            gups = n * n * T / ms / 1e6
+            # ALU roof: 9 flops per update (8 adds, 1 division); FP64 against the
+            # nominal 1.25 TFLOP/s of the part, FP32 against 152 SMs x 128 lanes x
+            # 2 flops x 2.07 GHz = 80.5 TFLOP/s (no measured FP64/FP32 peaks exist).
+            peak = 1250.0 if dn == "f64" else 80540.0
+            out[f"{name}_{dn}"] = {"ms": ms, "GUpdates/s": gups,
+                                   "roofline": {"bound": "alu", "achieved": 9 * gups, "peak": peak,
+                                                "unit": "GFLOP/s", "frac": 9 * gups / peak, "peak_kind": "nominal"},
                                    "params": {k: list(v) if isinstance(v, tuple) else v for k, v in (prm or {}).items()}}
         del base
     return out
