@@ -20,6 +20,8 @@ Contents
                      Gauss-Seidel 2-D (in place, 9-point average): the plain
                      loop nest and the recursive order over its skewed space
                      (C, ``oracle_gs.c``).
+  * ``fdtd2d``       FDTD-2D (three fields, a source row): the plain loop nest
+                     (C, ``oracle_fdtd.c``).
 """
 from __future__ import annotations
 
@@ -33,7 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "oracle_gs.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "oracle_gs.c"), os.path.join(_HERE, "oracle_fdtd.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +84,9 @@ def _load():
             lib.oracle_gs2d_tile_order.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _I64P, _I64P,
                                                    ctypes.c_int, _I64P, ctypes.c_int64]
             lib.oracle_gs2d_tile_order.restype = ctypes.c_int64
+            lib.oracle_fdtd2d.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _F64P, _F64P, _F64P,
+                                          _F64P, ctypes.c_int64]
+            lib.oracle_fdtd2d.restype = ctypes.c_int
             lib.oracle_pcot_order.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64, _I64P,
                                               _I64P, ctypes.c_int64]
             lib.oracle_pcot_order.restype = ctypes.c_int64
@@ -233,6 +238,22 @@ def gs2d_tile_order(n0, n1, T, tile, theta, wavefront=False):
     out = np.zeros((max(n, 1), 3), dtype=np.int64)
     lib.oracle_gs2d_tile_order(int(n0), int(n1), int(T), _ptr(tl, _I64P), _ptr(th, _I64P), wf, _ptr(out, _I64P), n)
     return out[:n]
+
+
+# ---- FDTD-2D (oracle_fdtd.c) --------------------------------------------
+
+def fdtd2d(ex, ey, hz, fict, T):
+    """T steps of FDTD-2D on nx x ny FP64 fields (fict: at least T source
+    values); returns new (ex, ey, hz)."""
+    ex, ey, hz = (np.ascontiguousarray(np.array(a, dtype=np.float64)) for a in (ex, ey, hz))
+    f = np.ascontiguousarray(np.array(fict, dtype=np.float64).reshape(-1))
+    if not (ex.shape == ey.shape == hz.shape) or (T > 0 and f.size < T):
+        raise ValueError("fdtd2d: field shapes differ or fict too short")
+    nx, ny = ex.shape
+    fp = _ptr(f, _F64P) if f.size else None
+    if _load().oracle_fdtd2d(nx, ny, ny, _ptr(ex, _F64P), _ptr(ey, _F64P), _ptr(hz, _F64P), fp, int(T)) != 0:
+        raise ValueError("oracle_fdtd2d: bad arguments")
+    return ex, ey, hz
 
 
 def interior(grid, sizes, radius=1, periodic=False):
