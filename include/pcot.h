@@ -400,6 +400,38 @@ pcot_status pcot_gs2d_plan_query(const int64_t *sizes, int64_t T, pcot_schedule 
                                  const pcot_tile_params *params, int32_t *lattice, int32_t *tile,
                                  int64_t *n_tiles, int32_t *queue, int32_t *deps, int64_t cap);
 
+/* ------------------------------------------------------------------------
+ * FDTD-2D (the two-dimensional FDTD kernel of the paper's benchmark suite,
+ * Sec. 5.1.2): three fields ex, ey, hz of nx x ny values (row stride s, the
+ * same for all three; strides {s, 1} or NULL for s = ny) advanced T steps.
+ * Step t:
+ *   ey[0][j] = fict[t];  ey[i][j] -= 0.5 * (hz[i][j] - hz[i-1][j])   (i >= 1)
+ *   ex[i][j] -= 0.5 * (hz[i][j] - hz[i][j-1])                          (j >= 1)
+ *   hz[i][j] -= 0.7 * (((ex[i][j+1] - ex[i][j]) + ey[i+1][j]) - ey[i][j])
+ *                                  (i <= nx-2, j <= ny-2; ex, ey of step t)
+ * each product and difference separately rounded in that order (no fused
+ * multiply-add): PCOT_F64 and PCOT_F64_EXACT are bitwise the loop nest in
+ * binary64, PCOT_F32 rounds the same operations to binary32.  fict: T values
+ * of the field type (device).  Schedules: PCOT_SWEEP one launch per step;
+ * PCOT_SLT tiles of tile[0] x tile[1] outputs advanced time_depth steps in
+ * shared memory (overlapped tiles, halo = time_depth; tiles at least
+ * time_depth wide; defaults 32 x 32 x 4 for FP64, 48 x 64 x 8 for FP32);
+ * PCOT_COT the same tiles as leaves of the recursive order over the
+ * (block, tile) lattice run by the persistent executor (cot_threshold =
+ * leaf in blocks, y-tiles, x-tiles; default 2, 256, 256), the remaining
+ * T mod time_depth steps as one single-level block.  The workspace (device,
+ * 256-byte aligned, pcot_fdtd2d_workspace_bytes) holds a second copy of the
+ * three fields and the recursive schedule's queue; the result is always in
+ * ex, ey, hz.  Asynchronous on `stream`; pcot_check reports device errors.
+ * ------------------------------------------------------------------------ */
+pcot_status pcot_fdtd2d_workspace_bytes(const int64_t *sizes, const int64_t *strides, int64_t T,
+                                        pcot_dtype dtype, pcot_schedule schedule,
+                                        const pcot_tile_params *params, size_t *bytes);
+pcot_status pcot_fdtd2d_run(pcot_handle h, void *ex, void *ey, void *hz, const void *fict, void *workspace,
+                            size_t workspace_bytes, const int64_t *sizes, const int64_t *strides, int64_t T,
+                            pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params *params,
+                            void *stream);
+
 /*
  * Number of kernels this handle has launched since it was created (sweep
  * steps, single-level blocks, persistent executors, ring copies, sums).

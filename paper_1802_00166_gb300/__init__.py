@@ -122,6 +122,10 @@ def _load():
                               ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_gs2d_plan_query": (S, [_I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _I32P,
                                      _I32P, _I64P, _I32P, _I32P, ctypes.c_int64]),
+        "pcot_fdtd2d_workspace_bytes": (S, [_I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_fdtd2d_run": (S, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64,
+                                ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
@@ -137,6 +141,7 @@ def _load():
 def exported_symbols():
     """Names declared in include/pcot.h that this binding marshals."""
     return ["pcot_gs2d_workspace_bytes", "pcot_gs2d_run", "pcot_gs2d_plan_query",
+            "pcot_fdtd2d_workspace_bytes", "pcot_fdtd2d_run",
             "pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
             "pcot_run_host", "pcot_check", "pcot_plan_query", "pcot_test_wait_timeout", "pcot_grid_sum",
             "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
@@ -266,6 +271,23 @@ def pcot_gs2d_plan_query(sizes, T, schedule, params=None, with_queue=True):
         out["queue"] = qq[:nt.value].copy()
         out["deps"] = dd[:ncell].copy()
     return out
+
+
+def pcot_fdtd2d_workspace_bytes(sizes, strides, T, dtype, schedule, params=None):
+    n = ctypes.c_size_t()
+    _chk(_load().pcot_fdtd2d_workspace_bytes(_p64(_i64(sizes)), _p64(_i64(strides)), int(T), int(dtype),
+                                             int(schedule), _params(params), ctypes.byref(n)),
+         "pcot_fdtd2d_workspace_bytes")
+    return n.value
+
+
+def pcot_fdtd2d_run(h, ex, ey, hz, fict, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,
+                    params=None, stream=None):
+    """FDTD-2D, the three device fields advanced in place (see include/pcot.h)."""
+    s, st = _i64(sizes), _i64(strides)
+    _chk(_load().pcot_fdtd2d_run(h, _ptr(ex), _ptr(ey), _ptr(hz), _ptr(fict), _ptr(workspace), int(workspace_bytes),
+                                 _p64(s), _p64(st), int(T), int(dtype), int(schedule), _params(params),
+                                 _stream(stream)), "pcot_fdtd2d_run")
 
 
 def pcot_run_host(h, host_grid, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,

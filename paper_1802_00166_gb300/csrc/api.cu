@@ -43,6 +43,14 @@ struct GsPlanCache {
     size_t image_bytes = 0, counts_bytes = 0;
 };
 
+// FDTD-2D recursive plan: queue and counters of the (block, tile) lattice.
+struct FdPlanCache {
+    int32_t lattice[4] = {0, 1, 1, 1};
+    std::vector<int32_t> queue, counts;
+    void* pinned = nullptr;
+    size_t image_bytes = 0, counts_bytes = 0;
+};
+
 }  // namespace
 
 struct pcot_plan {
@@ -55,6 +63,7 @@ struct pcot_plan {
     double* d_partials = nullptr;  // grid-sum partials
     std::map<std::string, CotPlanHost*> cot_cache;
     std::map<std::string, GsPlanCache*> gs_cache;
+    std::map<std::string, FdPlanCache*> fd_cache;
     uint64_t timeout_ns = kDefaultTimeoutNs;
     int64_t launches = 0;  // kernels launched by this handle
 };
@@ -389,6 +398,10 @@ pcot_status pcot_destroy(pcot_handle h) {
         delete kv.second;
     }
     for (auto& kv : h->gs_cache) {
+        if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+        delete kv.second;
+    }
+    for (auto& kv : h->fd_cache) {
         if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
         delete kv.second;
     }
@@ -1163,6 +1176,185 @@ pcot_status pcot_gs2d_run(pcot_handle h, void* grid, void* workspace, size_t wor
     if (nctas > q.ntiles) nctas = q.ntiles;
     PCOT_CUDA(launch_gs2d(dt, grid, q, (int)nctas, s));
     ++h->launches;
+    return PCOT_OK;
+}
+
+}  // extern "C"
+
+// ---- FDTD-2D ----------------------------------------------------------------
+namespace {
+
+bool fd_shape(pcot_schedule schedule, pcot_dtype dtype, const pcot_tile_params* p, int32_t* tile, int32_t* depth,
+              int64_t* theta) {
+    if (schedule != PCOT_SWEEP && schedule != PCOT_SLT && schedule != PCOT_COT) return false;
+    const bool f32 = dtype == PCOT_F32;
+    tile[0] = (p && p->tile[0] > 0) ? p->tile[0] : (f32 ? 48 : 32);
+    tile[1] = (p && p->tile[1] > 0) ? p->tile[1] : (f32 ? 64 : 32);
+    *depth = (p && p->time_depth > 0) ? p->time_depth : (f32 ? 8 : 4);
+    theta[0] = (p && p->cot_threshold[0] > 0) ? p->cot_threshold[0] : 2;
+    theta[1] = (p && p->cot_threshold[1] > 0) ? p->cot_threshold[1] : 256;
+    theta[2] = (p && p->cot_threshold[2] > 0) ? p->cot_threshold[2] : 256;
+    if (schedule == PCOT_SWEEP) return true;
+    // tiles at least as wide as the halo: a window meets only neighbouring tiles
+    if (tile[0] < *depth || tile[1] < *depth || *depth > 64 || tile[0] > 1024 || tile[1] > 1024) return false;
+    return true;
+}
+
+size_t fd_span_bytes(const int64_t* sizes, int64_t pitch, pcot_dtype dtype) {
+    return (size_t)((sizes[0] - 1) * pitch + sizes[1]) * (dtype == PCOT_F32 ? 4 : 8);
+}
+
+pcot_status fd_check_args(const int64_t* sizes, const int64_t* strides, int64_t T, pcot_dtype dtype, int64_t* pitch) {
+    if (!sizes || T < 0) return PCOT_ERR_INVALID_ARG;
+    if (dtype != PCOT_F32 && dtype != PCOT_F64 && dtype != PCOT_F64_EXACT) return PCOT_ERR_INVALID_ARG;
+    if (sizes[0] < 1 || sizes[1] < 1 || sizes[0] > (1LL << 30) || sizes[1] > (1LL << 30)) return PCOT_ERR_INVALID_ARG;
+    if (strides) {
+        if (strides[1] != 1) return PCOT_ERR_UNSUPPORTED;
+        if (strides[0] < sizes[1]) return PCOT_ERR_INVALID_ARG;
+        *pitch = strides[0];
+    } else {
+        *pitch = sizes[1];
+    }
+    return PCOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcot_status pcot_fdtd2d_workspace_bytes(const int64_t* sizes, const int64_t* strides, int64_t T, pcot_dtype dtype,
+                                        pcot_schedule schedule, const pcot_tile_params* params, size_t* bytes) {
+    if (!bytes) return PCOT_ERR_INVALID_ARG;
+    int64_t pitch = 0;
+    PCOT_TRY(fd_check_args(sizes, strides, T, dtype, &pitch));
+    int32_t tile[2], depth;
+    int64_t theta[3];
+    if (!fd_shape(schedule, dtype, params, tile, &depth, theta)) return PCOT_ERR_UNSUPPORTED;
+    size_t b = 3 * round_up(fd_span_bytes(sizes, pitch, dtype), kAlign);
+    if (schedule == PCOT_COT && T >= depth) {
+        const int64_t P = T / depth;
+        const int64_t L0 = (sizes[0] + tile[0] - 1) / tile[0], L1 = (sizes[1] + tile[1] - 1) / tile[1];
+        const int64_t n = P * L0 * L1;
+        if (n > (1LL << 28)) return PCOT_ERR_UNSUPPORTED;
+        b += kAlign + 2 * round_up((size_t)n * 4, kAlign);
+    }
+    *bytes = b;
+    return PCOT_OK;
+}
+
+pcot_status pcot_fdtd2d_run(pcot_handle h, void* ex, void* ey, void* hz, const void* fict, void* workspace,
+                            size_t workspace_bytes, const int64_t* sizes, const int64_t* strides, int64_t T,
+                            pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params, void* stream) {
+    if (!h || !ex || !ey || !hz || (T > 0 && !fict)) return PCOT_ERR_INVALID_ARG;
+    int64_t pitch = 0;
+    PCOT_TRY(fd_check_args(sizes, strides, T, dtype, &pitch));
+    int32_t tile[2], depth;
+    int64_t theta[3];
+    if (!fd_shape(schedule, dtype, params, tile, &depth, theta)) return PCOT_ERR_UNSUPPORTED;
+    const int es = dtype == PCOT_F32 ? 4 : 8;
+    if ((uintptr_t)ex % es || (uintptr_t)ey % es || (uintptr_t)hz % es || (uintptr_t)fict % es)
+        return PCOT_ERR_ALIGNMENT;
+    if (T == 0) return PCOT_OK;
+    size_t need = 0;
+    PCOT_TRY(pcot_fdtd2d_workspace_bytes(sizes, strides, T, dtype, schedule, params, &need));
+    if (!workspace || workspace_bytes < need) return PCOT_ERR_OOM;
+    if ((uintptr_t)workspace % kAlign) return PCOT_ERR_ALIGNMENT;
+    PCOT_TRY(ensure_device(h));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t span = fd_span_bytes(sizes, pitch, dtype), tw = round_up(span, kAlign);
+    unsigned char* ws = (unsigned char*)workspace;
+    void* f0[3] = {ex, ey, hz};
+    void* f1[3] = {ws, ws + tw, ws + 2 * tw};
+    FdDev q;
+    std::memset(&q, 0, sizeof(q));
+    q.nx = sizes[0];
+    q.ny = sizes[1];
+    q.pitch = pitch;
+    q.tile[0] = tile[0];
+    q.tile[1] = tile[1];
+    q.depth = depth;
+    const int dt = dtype == PCOT_F32 ? kF32 : kF64;
+    if (schedule != PCOT_SWEEP && fdtd2d_smem_bytes(dt, q) > 227 * 1024) return PCOT_ERR_UNSUPPORTED;
+    int cur = 0;  // copy holding the current fields
+    int64_t t = 0;
+    if (schedule == PCOT_SWEEP) {
+        for (; t < T; ++t) {
+            PCOT_CUDA(launch_fdtd2d_step(dt, q, cur ? f1 : f0, cur ? f0 : f1, fict, t, s));
+            ++h->launches;
+            cur ^= 1;
+        }
+    }
+    if (schedule == PCOT_COT && T >= depth) {
+        const int64_t P = T / depth;
+        const int64_t L[2] = {(sizes[0] + tile[0] - 1) / tile[0], (sizes[1] + tile[1] - 1) / tile[1]};
+        char key[160];
+        snprintf(key, sizeof(key), "%lld,%lld,%d,%d,%d,%lld,%lld,%lld,%lld", (long long)sizes[0], (long long)sizes[1],
+                 tile[0], tile[1], depth, (long long)P, (long long)theta[0], (long long)theta[1], (long long)theta[2]);
+        FdPlanCache* c = nullptr;
+        auto it = h->fd_cache.find(key);
+        if (it != h->fd_cache.end()) {
+            c = it->second;
+        } else {
+            c = new FdPlanCache();
+            c->queue = pcot_lattice_order((int)P, 2, L, theta, nullptr);
+            c->counts = lattice_dep_counts((int)P, 2, L);
+            c->lattice[0] = (int32_t)P;
+            c->lattice[1] = (int32_t)L[0];
+            c->lattice[2] = (int32_t)L[1];
+            c->counts_bytes = round_up(c->counts.size() * 4, kAlign);
+            c->image_bytes = kAlign + c->counts_bytes + round_up(c->queue.size() * 4, kAlign);
+            void* p = nullptr;
+            cudaError_t e = cudaMallocHost(&p, c->image_bytes);
+            if (e != cudaSuccess) {
+                delete c;
+                return from_cuda(e);
+            }
+            std::memset(p, 0, c->image_bytes);
+            std::memcpy((unsigned char*)p + kAlign, c->counts.data(), c->counts.size() * 4);
+            std::memcpy((unsigned char*)p + kAlign + c->counts_bytes, c->queue.data(), c->queue.size() * 4);
+            c->pinned = p;
+            if (h->fd_cache.size() >= 16) {
+                for (auto& kv : h->fd_cache) {
+                    if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+                    delete kv.second;
+                }
+                h->fd_cache.clear();
+            }
+            h->fd_cache[key] = c;
+        }
+        unsigned char* img = ws + 3 * tw;
+        PCOT_CUDA(cudaMemcpyAsync(img, c->pinned, c->image_bytes, cudaMemcpyHostToDevice, s));
+        CotDev cd;
+        std::memset(&cd, 0, sizeof(cd));
+        cd.head = (int32_t*)img;
+        cd.counts = (int32_t*)(img + kAlign);
+        cd.queue = (const int32_t*)(img + kAlign + c->counts_bytes);
+        cd.ntiles = (int64_t)c->queue.size();
+        for (int i = 0; i < 4; ++i) cd.lattice[i] = c->lattice[i];
+        cd.status = h->d_status;
+        cd.timeout_ns = h->timeout_ns;
+        const int per_sm = fdtd2d_cot_ctas_per_sm(dt, q);
+        if (per_sm < 1) return PCOT_ERR_UNSUPPORTED;
+        int64_t nctas = (int64_t)per_sm * h->num_sms;
+        const int64_t cap = std::max<int64_t>(h->num_sms, L[0] * L[1] * 2 / 5);  // as for the stencils
+        if (nctas > cap) nctas = cap;
+        if (nctas > cd.ntiles) nctas = cd.ntiles;
+        PCOT_CUDA(launch_fdtd2d_cot(dt, q, cd, f0, f1, fict, (int)nctas, s));
+        ++h->launches;
+        t = P * depth;
+        cur = (int)(P & 1);
+    }
+    // single-level blocks (the whole run for PCOT_SLT, the tail for PCOT_COT)
+    while (t < T) {
+        const int k = (int)std::min<int64_t>(depth, T - t);
+        PCOT_CUDA(launch_fdtd2d_block(dt, q, cur ? f1 : f0, cur ? f0 : f1, fict, t, k, s));
+        ++h->launches;
+        cur ^= 1;
+        t += k;
+    }
+    if (cur) {  // the result is in the workspace copy
+        for (int a = 0; a < 3; ++a) PCOT_CUDA(cudaMemcpyAsync(f0[a], f1[a], span, cudaMemcpyDeviceToDevice, s));
+    }
     return PCOT_OK;
 }
 

@@ -62,6 +62,22 @@ size_t gs2d_smem_bytes(int dtype, const GsDev& q);
 int gs2d_ctas_per_sm(int dtype, const GsDev& q);
 cudaError_t launch_gs2d(int dtype, void* grid, const GsDev& q, int nctas, cudaStream_t s);
 
+// ---- k_fdtd2d.cu: FDTD-2D (three fields, two copies) ----
+struct FdDev {
+    int64_t nx, ny;        // field rows and columns
+    int64_t pitch;         // row stride (elements), the same for the three fields
+    int32_t tile[2];       // output tile H x W of the tiled schedules
+    int32_t depth;         // steps per block K (the shared-memory window has a halo of K)
+};
+size_t fdtd2d_smem_bytes(int dtype, const FdDev& q);
+int fdtd2d_cot_ctas_per_sm(int dtype, const FdDev& q);
+cudaError_t launch_fdtd2d_step(int dtype, const FdDev& q, void* const* src, void* const* dst, const void* fict,
+                               int64_t t, cudaStream_t s);
+cudaError_t launch_fdtd2d_block(int dtype, const FdDev& q, void* const* src, void* const* dst, const void* fict,
+                                int64_t t0, int k, cudaStream_t s);
+cudaError_t launch_fdtd2d_cot(int dtype, const FdDev& q, const CotDev& c, void* const* f0, void* const* f1,
+                              const void* fict, int nctas, cudaStream_t s);
+
 // ---- k_sweep.cu ----
 cudaError_t launch_sweep(const LaunchCtx& L, const void* src, void* dst);
 cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst);
