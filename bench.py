@@ -411,13 +411,15 @@ def run_gpu(args):
                                 "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
     if args.schedules and rank == 0:
         line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
-    if (args.batched or args.gs2d) and rank == 0:
+    if (args.batched or args.gs2d or args.fdtd2d) and rank == 0:
         del base, wsbuf, host
         torch.cuda.empty_cache()
     if args.batched and rank == 0:
         line["batched"] = run_batched(pcot, stream, args.steps)
     if args.gs2d and rank == 0:
         line["gs2d"] = run_gs2d(pcot, h, stream, args.steps)
+    if args.fdtd2d and rank == 0:
+        line["fdtd2d"] = run_fdtd2d(pcot, h, stream, args.steps)
     pcot.pcot_destroy(h)
     if rank == 0:
         print(json.dumps(line))
@@ -474,6 +476,67 @@ def run_gs2d(pcot, h, stream, steps):
                                                 "unit": "GFLOP/s", "frac": 9 * gups / peak, "peak_kind": "nominal"},
                                    "params": {k: list(v) if isinstance(v, tuple) else v for k, v in (prm or {}).items()}}
         del base
+    return out
+
+
+FDTD2D = {"n": 2000, "T": 500, "slt_f64": {"tile": (32, 64), "time_depth": 4},
+          "slt_f32": {"tile": (32, 64), "time_depth": 4},
+          "cot_f64": {"tile": (32, 32), "time_depth": 4, "cot_threshold": (2, 256, 256)},
+          "cot_f32": {"tile": (48, 64), "time_depth": 8, "cot_threshold": (2, 256, 256)}}
+
+
+def run_fdtd2d(pcot, h, stream, steps):
+    """FDTD-2D at the paper's size (2000^2, T = 500; Table 2): the three fields
+    advanced on the device under the sweep, single-level and recursive
+    schedules, FP64 (bitwise the loop nest) and FP32; CUDA events, inputs
+    resident.  Roofline: FP64 against the DP pipe (11 flops per update); FP32
+    against HBM with one read and one write of the three fields per pass (a
+    pass is one step for the sweep, k steps for the tiles)."""
+    import torch
+    n, T = FDTD2D["n"], FDTD2D["T"]
+    peak_bw, _ = _peaks()
+    out = {"workload": f"fdtd2d {n}x{n} T={T}", "unit": "GUpdates/s"}
+    for dtype, dn in ((pcot.PCOT_F64, "f64"), (pcot.PCOT_F32, "f32")):
+        tdt = torch.float32 if dtype == pcot.PCOT_F32 else torch.float64
+        esz = 4 if dtype == pcot.PCOT_F32 else 8
+        f = [torch.rand(n * n, dtype=tdt, device="cuda") for _ in range(3)]
+        fict = torch.rand(T, dtype=tdt, device="cuda")
+        for name, sched, prm in (("sweep", pcot.PCOT_SWEEP, None), ("slt", pcot.PCOT_SLT, FDTD2D["slt_" + dn]),
+                                 ("cot", pcot.PCOT_COT, FDTD2D["cot_" + dn])):
+            p = pcot.tile_params(**prm) if prm else None
+            nb = pcot.pcot_fdtd2d_workspace_bytes((n, n), None, T, dtype, sched, p)
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            run = lambda: pcot.pcot_fdtd2d_run(h, f[0].data_ptr(), f[1].data_ptr(), f[2].data_ptr(), fict.data_ptr(),
+                                               ws.data_ptr(), nb, (n, n), None, T, dtype, sched, p, stream)
+            for _ in range(2):
+                run()
+            torch.cuda.synchronize()
+            reps = max(1, min(steps, 3))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = pcot.pcot_check(h, stream)
+            if st != pcot.PCOT_OK:
+                raise pcot.PcotError(st, "fdtd2d " + name)
+            ms = e0.elapsed_time(e1) / reps
+            k = 1 if prm is None else prm["time_depth"]
+            gups = n * n * T / ms / 1e6
+            if dn == "f64":
+                # FP64 is bound by the DP pipe: 11 flops per update (3 + 3 + 5)
+                # against the part's nominal 1.25 TFLOP/s
+                roof = {"bound": "alu", "achieved": 11 * gups, "peak": 1250.0, "unit": "GFLOP/s",
+                        "frac": 11 * gups / 1250.0, "peak_kind": "nominal"}
+            else:
+                alg = math.ceil(T / k) * 2.0 * 3 * n * n * esz
+                roof = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak_bw, "unit": "GB/s",
+                        "frac": alg / (ms / 1e3) / 1e9 / peak_bw}
+            out[f"{name}_{dn}"] = {"ms": ms, "GUpdates/s": gups, "roofline": roof,
+                                   "params": {a: list(v) if isinstance(v, tuple) else v for a, v in (prm or {}).items()}}
+        del f, fict
     return out
 
 
@@ -616,6 +679,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true", help="also time the 256-grid batched persistent launch")
     ap.add_argument("--gs2d", action="store_true", help="also time Gauss-Seidel 2-D at the paper's size")
+    ap.add_argument("--fdtd2d", action="store_true", help="also time FDTD-2D at the paper's size")
     ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
     ap.add_argument("--case-n", type=int, default=8192)

@@ -93,10 +93,14 @@ __device__ __forceinline__ void fdtd_tile(const FdDev& q, const T* __restrict__ 
     T* sy = sm + cells;
     T* sh = sm + 2 * cells;
     const int64_t wi = i0 - K, wj = j0 - K;  // window origin (global)
+    // Each thread walks the window's cells tid, tid + n, ... in row-major
+    // order; the (row, column) of the next cell follows by a fixed step, so the
+    // loops carry no index division.
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const int drow = nthr / Ws, dcol = nthr - drow * Ws;
+    const int li0 = tid / Ws, lj0 = tid - li0 * Ws;
     const int64_t s = q.pitch;
-    for (int c = tid; c < cells; c += nthr) {
-        const int li = c / Ws, lj = c - li * Ws;
+    for (int c = tid, li = li0, lj = lj0; c < cells; c += nthr) {
         const int64_t i = wi + li, j = wj + lj;
         T vx = T(0), vy = T(0), vh = T(0);
         if (i >= 0 && i < q.nx && j >= 0 && j < q.ny) {
@@ -114,39 +118,60 @@ __device__ __forceinline__ void fdtd_tile(const FdDev& q, const T* __restrict__ 
         sx[c] = vx;
         sy[c] = vy;
         sh[c] = vh;
+        li += drow;
+        lj += dcol;
+        if (lj >= Ws) {
+            lj -= Ws;
+            ++li;
+        }
     }
     __syncthreads();
     for (int st = 0; st < k; ++st) {
         const T src = fict[t0 + st];
         // electric fields from the magnetic field of the previous step
-        for (int c = tid; c < cells; c += nthr) {
-            const int li = c / Ws, lj = c - li * Ws;
+        for (int c = tid, li = li0, lj = lj0; c < cells; c += nthr) {
             const int64_t i = wi + li, j = wj + lj;
-            if (i < 0 || i >= q.nx || j < 0 || j >= q.ny) continue;
-            if (i == 0) sy[c] = src;
-            else if (li >= 1) sy[c] = e_upd(sy[c], sh[c], sh[c - Ws]);
-            if (j >= 1 && lj >= 1) sx[c] = e_upd(sx[c], sh[c], sh[c - 1]);
+            if (i >= 0 && i < q.nx && j >= 0 && j < q.ny) {
+                if (i == 0) sy[c] = src;
+                else if (li >= 1) sy[c] = e_upd(sy[c], sh[c], sh[c - Ws]);
+                if (j >= 1 && lj >= 1) sx[c] = e_upd(sx[c], sh[c], sh[c - 1]);
+            }
+            li += drow;
+            lj += dcol;
+            if (lj >= Ws) {
+                lj -= Ws;
+                ++li;
+            }
         }
         __syncthreads();
         // magnetic field from the new electric fields
-        for (int c = tid; c < cells; c += nthr) {
-            const int li = c / Ws, lj = c - li * Ws;
+        for (int c = tid, li = li0, lj = lj0; c < cells; c += nthr) {
             const int64_t i = wi + li, j = wj + lj;
-            if (i < 0 || i > q.nx - 2 || j < 0 || j > q.ny - 2 || li + 1 >= Hs || lj + 1 >= Ws) continue;
-            sh[c] = h_upd(sh[c], sx[c + 1], sx[c], sy[c + Ws], sy[c]);
+            if (i >= 0 && i <= q.nx - 2 && j >= 0 && j <= q.ny - 2 && li + 1 < Hs && lj + 1 < Ws)
+                sh[c] = h_upd(sh[c], sx[c + 1], sx[c], sy[c + Ws], sy[c]);
+            li += drow;
+            lj += dcol;
+            if (lj >= Ws) {
+                lj -= Ws;
+                ++li;
+            }
         }
         __syncthreads();
     }
     // the tile's outputs (valid: k cells from every window edge)
-    for (int c = tid; c < H * W; c += nthr) {
-        const int oi = c / W, oj = c - oi * W;
-        const int64_t i = i0 + oi, j = j0 + oj;
-        if (i >= q.nx || j >= q.ny) continue;
-        const int w = (oi + K) * Ws + (oj + K);
-        const int64_t g = i * s + j;
-        ex2[g] = sx[w];
-        ey2[g] = sy[w];
-        hz2[g] = sh[w];
+    const int lane = tid & 31, wrp = tid >> 5, nw = nthr >> 5;
+    for (int oi = wrp; oi < H; oi += nw) {
+        const int64_t i = i0 + oi;
+        if (i >= q.nx) break;
+        for (int oj = lane; oj < W; oj += 32) {
+            const int64_t j = j0 + oj;
+            if (j >= q.ny) break;
+            const int w = (oi + K) * Ws + (oj + K);
+            const int64_t g = i * s + j;
+            ex2[g] = sx[w];
+            ey2[g] = sy[w];
+            hz2[g] = sh[w];
+        }
     }
 }
 
