@@ -38,6 +38,8 @@ UNIT = "GUpdates/s"
 BEST = {"schedule": "cot", "tile": (80, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
 BEST_SLT = {"schedule": "slt", "tile": (40, 112), "time_depth": 4, "cot_threshold": (2, 256, 256)}
 BATCH = {"tile": (96, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
+# Depths (with their best tile heights) scanned beside the headline.
+DEPTH_SCAN = [(2, (80, 112)), (4, (80, 112)), (6, (96, 112)), (8, (80, 112))]
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
 
 
@@ -394,6 +396,32 @@ def run_gpu(args):
             "launch_ms": launch_s * 1e3, "launches_timed_per_step": n_dom,
             "model": "per time block of depth k: one read + one write of the 8192^2 fp32 grid"}
 
+    # The temporal-blocking roof rises with the block depth k (one HBM pass per
+    # k steps), so a deeper block can be faster yet reach a smaller fraction of
+    # its own roof.  Scan the recursive schedule's depths on the same grid and
+    # report, per depth, the throughput and the fraction of that depth's roof.
+    if rank == 0 and sched == pcot.PCOT_COT and not args.schedule:
+        scan = []
+        for kd, tl in DEPTH_SCAN:
+            prm = pcot.tile_params(tile=tl, time_depth=kd, cot_threshold=BEST["cot_threshold"])
+            nbk = pcot.pcot_workspace_bytes(h, sizes, strides, T_STEPS, pcot.PCOT_F32, sched, prm)
+            wsk = torch.empty(nbk, dtype=torch.uint8, device="cuda")
+            runk = lambda: pcot.pcot_run(h, base.data_ptr(), wsk.data_ptr(), nbk, sizes, strides, T_STEPS,
+                                         pcot.PCOT_F32, sched, prm, stream)
+            runk()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                runk()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msk = e0.elapsed_time(e1) / 3
+            t_roof = math.ceil(T_STEPS / kd) * grid_bytes / (peak * 1e9) * 1e3
+            scan.append({"time_depth": kd, "tile": list(tl), "ms": msk,
+                         "GUpdates/s": N_SIDE * N_SIDE * T_STEPS / msk / 1e6, "roofline_frac": t_roof / msk})
+            del wsk
+        roof["by_depth"] = scan
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -649,12 +677,28 @@ def run_profile_case(args):
     from paper_1802_00166_gb300 import build as pbuild
     pbuild.build()
     n, T = args.case_n, args.case_T
-    H, W = (int(v) for v in args.case_tile.split(","))
     th = tuple(int(v) for v in args.case_theta.split(","))
+    sched = pcot.SCHEDULES[args.profile_case]
+    if args.case_dims == 3:
+        # Jacobi-3D 7-point, periodic n^3 grid (the 3-D workload's stencil)
+        tile = tuple(int(v) for v in args.case_tile.split(","))
+        h = pcot.pcot_create(3, 1, [0.4] + [0.1] * 6, pcot.PCOT_PERIODIC)
+        base = torch.rand(n ** 3, device="cuda")
+        p = pcot.tile_params(tile=tile, time_depth=args.case_k)
+        nb = pcot.pcot_workspace_bytes(h, (n, n, n), None, T, pcot.PCOT_F32, sched, p)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        for _ in range(args.case_runs):
+            pcot.pcot_run(h, base.data_ptr(), ws.data_ptr(), nb, (n, n, n), None, T, pcot.PCOT_F32, sched, p)
+        st = pcot.pcot_check(h)
+        pcot.pcot_destroy(h)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "profile case")
+        print(f"ok 3-D {args.profile_case} n={n} T={T} k={args.case_k} tile={tile}")
+        return 0
+    H, W = (int(v) for v in args.case_tile.split(","))
     h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
     pitch = ((n + 2 + 31) // 32) * 32
     base = torch.rand((n + 2) * pitch, device="cuda")
-    sched = pcot.SCHEDULES[args.profile_case]
     p = pcot.tile_params(tile=(H, W), time_depth=args.case_k, cot_threshold=th)
     nb = pcot.pcot_workspace_bytes(h, (n, n), (pitch, 1), T, pcot.PCOT_F32, sched, p)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
@@ -682,6 +726,7 @@ def main():
     ap.add_argument("--fdtd2d", action="store_true", help="also time FDTD-2D at the paper's size")
     ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
+    ap.add_argument("--case-dims", type=int, default=2, choices=[2, 3])
     ap.add_argument("--case-n", type=int, default=8192)
     ap.add_argument("--case-T", type=int, default=64)
     ap.add_argument("--case-k", type=int, default=8)
