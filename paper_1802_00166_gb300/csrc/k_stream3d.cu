@@ -40,7 +40,7 @@ struct Shape {
 
 // Register budget per thread: the stage rings hold 3*K*RY*E values.
 template <class T, int K>
-constexpr int kRegBudget3 = sizeof(T) == 8 ? (K <= 1 ? 168 : 232) : (K <= 1 ? 96 : (K <= 2 ? 128 : 168));
+constexpr int kRegBudget3 = sizeof(T) == 8 ? (K <= 1 ? 168 : 232) : (K <= 1 ? 104 : (K <= 2 ? 128 : 168));
 
 // Warps per CTA the budget allows within the 64K-register file.
 inline int max_warps_for(int dtype, int depth) {
@@ -112,7 +112,13 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     const bool warp_xint = __all_sync(kFull, lane_xint);
     const bool brick_ok = per || (brick_int && warp_xint);  // no pass-through inside this brick
 
-    auto load_row = [&](int64_t zi, int r, T (&v)[E]) {
+    // Row offsets of the brick inside a plane (computed once per tile).
+    int64_t yoff[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) yoff[r] = ysrc[r] * Py;
+
+    // The brick's rows of input plane zi (plane index and bounds once per plane).
+    auto load_plane = [&](int64_t zi, T (&v)[RY][E]) {
         int64_t zs;
         bool zin;
         if (per) {
@@ -122,19 +128,23 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             zs = zi;
             zin = zi >= 0 && zi < ez;
         }
-        if (!zin || !yin[r]) {
-            v[0] = T(0);
-            v[1] = T(0);
-            return;
-        }
-        const T* rowp = src + zs * Pz + ysrc[r] * Py;
-        if (lvec) {
-            const V q = gload<CG>(reinterpret_cast<const V*>(rowp + col[0]));
-            v[0] = q.x;
-            v[1] = q.y;
-        } else {
+        const T* plane = src + zs * Pz;
 #pragma unroll
-            for (int j = 0; j < E; ++j) v[j] = inb[j] ? gload<CG>(rowp + col[j]) : T(0);
+        for (int r = 0; r < RY; ++r) {
+            if (!zin || !yin[r]) {
+                v[r][0] = T(0);
+                v[r][1] = T(0);
+                continue;
+            }
+            const T* rowp = plane + yoff[r];
+            if (lvec) {
+                const V q = gload<CG>(reinterpret_cast<const V*>(rowp + col[0]));
+                v[r][0] = q.x;
+                v[r][1] = q.y;
+            } else {
+#pragma unroll
+                for (int j = 0; j < E; ++j) v[r][j] = inb[j] ? gload<CG>(rowp + col[j]) : T(0);
+            }
         }
     };
 
@@ -156,8 +166,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
 
     const int64_t zbeg = z0 - K, zend = z0 + Hz + K;
     T pf[RY][E];
-#pragma unroll
-    for (int r = 0; r < RY; ++r) load_row(zbeg, r, pf[r]);
+    load_plane(zbeg, pf);
     int buf = 0;
 
     auto step = [&](auto Uc, int64_t zi) {
@@ -168,10 +177,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             R[0][SN][r][0] = pf[r][0];
             R[0][SN][r][1] = pf[r][1];
         }
-        if (zi + 1 < zend) {
-#pragma unroll
-            for (int r = 0; r < RY; ++r) load_row(zi + 1, r, pf[r]);
-        }
+        if (zi + 1 < zend) load_plane(zi + 1, pf);
         T* smb = sm + buf * buf_stride;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
@@ -229,10 +235,11 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         const int64_t zo = zi - K;
         const bool zok = zo >= z0 && zo < z0 + Hz && (per ? zo < nz : (zo >= 1 && zo <= nz));
         if (zok) {
+            T* const row0 = dst + zo * Pz + ybase * Py;
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 if (!ystore[r]) continue;
-                T* rowp = dst + zo * Pz + (ybase + r) * Py;
+                T* rowp = row0 + r * Py;
                 if (svec) {
                     V q;
                     q.x = out[r][0];
