@@ -22,6 +22,11 @@ Contents
                      (C, ``oracle_gs.c``).
   * ``fdtd2d``       FDTD-2D (three fields, a source row): the plain loop nest
                      (C, ``oracle_fdtd.c``).
+  * ``lu`` / ``cholesky`` / ``la_pcot`` / ``la_box_empty`` / ``la_tile_order``
+                     LU (no pivoting) and Cholesky factorizations: the plain
+                     loops and the recursive order over their (k, i, j)
+                     space, whose bounding box holds empty orthants (C,
+                     ``oracle_la.c``).
 """
 from __future__ import annotations
 
@@ -35,7 +40,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "oracle_gs.c"), os.path.join(_HERE, "oracle_fdtd.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "oracle_gs.c"), os.path.join(_HERE, "oracle_fdtd.c"),
+         os.path.join(_HERE, "oracle_la.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -50,7 +56,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-shared", "-fPIC", "-o", _LIB + ".tmp"] + _SRCS
+           "-shared", "-fPIC", "-o", _LIB + ".tmp"] + _SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -90,6 +96,18 @@ def _load():
             lib.oracle_pcot_order.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, ctypes.c_int64, _I64P,
                                               _I64P, ctypes.c_int64]
             lib.oracle_pcot_order.restype = ctypes.c_int64
+            lib.oracle_lu.argtypes = [ctypes.c_int64, ctypes.c_int64, _F64P, ctypes.c_int]
+            lib.oracle_lu.restype = ctypes.c_int
+            lib.oracle_cholesky.argtypes = [ctypes.c_int64, ctypes.c_int64, _F64P, ctypes.c_int]
+            lib.oracle_cholesky.restype = ctypes.c_int
+            lib.oracle_la_box_empty.argtypes = [ctypes.c_int, ctypes.c_int64, _I64P, _I64P]
+            lib.oracle_la_box_empty.restype = ctypes.c_int
+            lib.oracle_la_pcot.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _F64P, ctypes.c_int,
+                                           _I64P, _I64P]
+            lib.oracle_la_pcot.restype = ctypes.c_int
+            lib.oracle_la_tile_order.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _I64P, ctypes.c_int,
+                                                 _I64P, ctypes.c_int64]
+            lib.oracle_la_tile_order.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -254,6 +272,72 @@ def fdtd2d(ex, ey, hz, fict, T):
     if _load().oracle_fdtd2d(nx, ny, ny, _ptr(ex, _F64P), _ptr(ey, _F64P), _ptr(hz, _F64P), fp, int(T)) != 0:
         raise ValueError("oracle_fdtd2d: bad arguments")
     return ex, ey, hz
+
+
+# ---- LU and Cholesky (oracle_la.c) --------------------------------------
+
+LA_KINDS = {"lu": 0, "cholesky": 1}
+
+
+def _square(A):
+    a = np.ascontiguousarray(np.array(A, dtype=np.float64))
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("expected a square matrix")
+    return a
+
+
+def lu(A, fused=False):
+    """In-place LU without pivoting of a square FP64 matrix (unit lower L
+    below the diagonal, U on and above it); returns a new array."""
+    a = _square(A)
+    n = a.shape[0]
+    if _load().oracle_lu(n, n, _ptr(a, _F64P), int(bool(fused))) != 0:
+        raise ValueError("oracle_lu: bad arguments")
+    return a
+
+
+def cholesky(A, fused=False):
+    """In-place lower Cholesky factor of a square FP64 matrix (the strict
+    upper triangle is returned unchanged); returns a new array."""
+    a = _square(A)
+    n = a.shape[0]
+    if _load().oracle_cholesky(n, n, _ptr(a, _F64P), int(bool(fused))) != 0:
+        raise ValueError("oracle_cholesky: bad arguments")
+    return a
+
+
+def la_pcot(kind, A, leaf, fused=False, return_stats=False):
+    """The factorization `kind` ("lu" or "cholesky") in the recursive order
+    over its (k, i, j) space with leaf box `leaf` (three widths)."""
+    a = _square(A)
+    n = a.shape[0]
+    lf = _i64(leaf)
+    st = np.zeros(4, dtype=np.int64)
+    if _load().oracle_la_pcot(LA_KINDS[kind], n, n, _ptr(a, _F64P), int(bool(fused)), _ptr(lf, _I64P),
+                              _ptr(st, _I64P)) != 0:
+        raise ValueError("oracle_la_pcot: bad arguments")
+    if return_stats:
+        return a, dict(leaves=int(st[0]), zero_exits=int(st[1]), empty_exits=int(st[2]), points=int(st[3]))
+    return a
+
+
+def la_box_empty(kind, n, lo, hi):
+    """Exact emptiness of an inclusive box of (k, i, j) points."""
+    return bool(_load().oracle_la_box_empty(LA_KINDS[kind], int(n), _ptr(_i64(lo), _I64P), _ptr(_i64(hi), _I64P)))
+
+
+def la_tile_order(kind, n, b, theta=(1, 1, 1), recursive=True):
+    """Non-empty tiles (kb, ib, jb) of b x b x b tiles in execution order, as
+    a (count, 3) int64 array."""
+    lib = _load()
+    th = _i64(theta)
+    r = 1 if recursive else 0
+    cnt = lib.oracle_la_tile_order(LA_KINDS[kind], int(n), int(b), _ptr(th, _I64P), r, None, 0)
+    if cnt < 0:
+        raise ValueError("oracle_la_tile_order: bad arguments")
+    out = np.zeros((max(cnt, 1), 3), dtype=np.int64)
+    lib.oracle_la_tile_order(LA_KINDS[kind], int(n), int(b), _ptr(th, _I64P), r, _ptr(out, _I64P), cnt)
+    return out[:cnt]
 
 
 def interior(grid, sizes, radius=1, periodic=False):
