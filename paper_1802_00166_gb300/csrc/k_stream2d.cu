@@ -43,14 +43,25 @@ struct Shape {
     static constexpr int Wo = 32 * E - 2 * Kp;          // output columns per warp
 };
 
-// Interior FP32 warps fed by TMA evaluate the update two cells at a time with the packed
+// FP32 warps fed by TMA evaluate the update two cells at a time with the packed
 // f32x2 multiply and fused multiply-add (same per-cell rounding and operand
 // order as the scalar path, so the results are bitwise unchanged).  A lane's
 // four columns c0..c3 are stored as the pairs (c0, c2) and (c1, c3): then the
 // west neighbours of (c1, c3) and the east neighbours of (c0, c2) are existing
 // pairs, and only (w, c1) and (c2, e) have to be assembled per stage.
-template <class T, bool EXACT, bool CHECK, bool TMA>
-constexpr bool kPacked = std::is_same<T, float>::value && !EXACT && !CHECK && TMA;
+//
+// Boundary warps (CHECK: Dirichlet pass-through, partial stores) of the
+// launch-per-block kernels run the same unrolled TMA loop as interior warps:
+// a boundary tile row ends every single-level launch, so its speed sets the
+// launch's tail (3.3x the instructions per row in a compact body made it
+// 1.3-1.6x slower).  The persistent kernels interleave boundary tiles with
+// interior ones and keep the compact body: a second unrolled body cost them
+// more in instruction fetch than it saved (COT at k = 8: -11%).
+template <bool CG>
+constexpr bool kUnrolledCheck = !CG;
+
+template <class T, bool EXACT, bool CHECK, bool TMA, bool CG>
+constexpr bool kPacked = std::is_same<T, float>::value && !EXACT && TMA && (!CHECK || kUnrolledCheck<CG>);
 
 // Register slot of lane column j (identity unless packed).
 template <bool PK>
@@ -184,7 +195,7 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
     }
     const bool warp_xint = __all_sync(kFull, xint[0] && xint[E - 1]);
 
-    constexpr bool PK = kPacked<T, EXACT, CHECK, TMA>;
+    constexpr bool PK = kPacked<T, EXACT, CHECK, TMA, CG>;
     static_assert(!PK || E == 4, "packed path assumes four columns per lane");
     float2 k2[5];
 #pragma unroll
@@ -266,12 +277,14 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 }
             }
             if constexpr (CHECK) {
+                // Dirichlet pass-through; slot j holds column slot_of(j)
+                // (the slot map is its own inverse)
                 const int rr = i - s - 1;
                 const bool rint = rr >= rlo && rr <= rhi;
                 if (!(rint && warp_xint)) {
 #pragma unroll
                     for (int j = 0; j < E; ++j)
-                        if (!(rint && xint[j])) out[j] = R[s][SB][j];
+                        if (!(rint && xint[slot_of<PK>(j)])) out[j] = R[s][SB][j];
                 }
             }
             if (s + 1 < K) {
@@ -299,7 +312,8 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
         }
     };
 
-    // One step of the general loop (boundary warps, plain-load input).
+    // One step of the general loop (plain-load input; boundary warps of the
+    // persistent kernels).
     auto step = [&](auto Uc, int i) {
         constexpr int U = decltype(Uc)::value;
         constexpr int SN = (U + 2) % 3;
@@ -331,9 +345,10 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
         store(i, dst_row0 + (int64_t)i * P, out);
     };
 
-    if constexpr (CHECK) {
-        // Boundary warps (a few per grid): one compact body and explicit
-        // rotation of the rings, to keep the instruction footprint small.
+    if constexpr (CHECK && !(TMA && kUnrolledCheck<CG>)) {
+        // Boundary warps on plain loads or in a persistent kernel: one compact
+        // body and explicit rotation of the rings, to keep the instruction
+        // footprint small.
         for (int i = 0; i < nrows; ++i) {
             step(IC<0>{}, i);
 #pragma unroll
@@ -354,10 +369,12 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             }
         }
     } else if constexpr (TMA) {
-        // Interior warps fed by TMA: one ring fill of kRingRows = 3 rows per
-        // iteration, so the fill's wait and release and the phases of the
-        // register ring are fixed at compile time.  The last fill's rows past
-        // H + 2K are computed from real or zero-filled rows and never stored.
+        // Warps fed by TMA: one ring fill of kRingRows = 3 rows per iteration,
+        // so the fill's wait and release and the phases of the register ring
+        // are fixed at compile time.  The last fill's rows past H + 2K are
+        // computed from real or zero-filled rows and never stored.  Boundary
+        // warps of the single-level kernel run the same loop with the
+        // pass-through in stages().
         static_assert(kRingRows == 3, "one fill per cycle of the register ring");
         auto fstep = [&](auto Uc, int ii, const T* src_row, T* out_row) {
             constexpr int SN = (decltype(Uc)::value + 2) % 3;
