@@ -432,6 +432,59 @@ pcot_status pcot_fdtd2d_run(pcot_handle h, void *ex, void *ey, void *hz, const v
                             pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params *params,
                             void *stream);
 
+/* ------------------------------------------------------------------------
+ * LU and Cholesky factorizations (the linear-algebra kernels of the paper's
+ * benchmark suite, Sec. 5.1.2), whose iteration spaces are triangular: the
+ * recursion over their bounding box skips empty orthants (Sec. 4.3).
+ *
+ * A: n x n binary64 matrix (device, 8-byte aligned), row-major with row
+ * stride lda >= n elements, factored in place.
+ *   PCOT_LA_LU        Gaussian elimination without pivoting: for k = 0..n-1,
+ *                     A[i][k] /= A[k][k] (i > k), then
+ *                     A[i][j] -= A[i][k] * A[k][j] (i, j > k); the result
+ *                     holds the unit lower factor below the diagonal and the
+ *                     upper factor on and above it.  No pivoting: a zero or
+ *                     tiny pivot gives infinities or NaNs, as in the loops.
+ *   PCOT_LA_CHOLESKY  lower Cholesky factor: for k = 0..n-1,
+ *                     A[k][k] = sqrt(A[k][k]), A[i][k] /= A[k][k] (i > k),
+ *                     A[i][j] -= A[i][k] * A[j][k] (k < j <= i); only the
+ *                     lower triangle is read or written.
+ * Each element receives its updates for k ascending, then its division (or
+ * square root), so every schedule is bitwise the loops above: PCOT_F64 with
+ * each update one fused multiply-add, PCOT_F64_EXACT with a rounded product
+ * and a rounded difference.  PCOT_F32 is not supported.
+ * Schedules: PCOT_SWEEP the plain loop over k (two launches per k);
+ * PCOT_SLT tiles of b x b x b points of the (k, i, j) space, one launch each
+ * for the diagonal tile, the panels and the updates of every block step;
+ * PCOT_COT the same tiles in the recursive order over the tile lattice
+ * (orthants with equal numbers of upper halves side by side, leaves
+ * lexicographic), run by a persistent kernel that waits (bounded) on
+ * per-tile dependency counters.  params: tile[0] = b (32 or 64, default 64),
+ * cot_threshold[0..2] = recursion leaf in tiles along (k, i, j) (default
+ * 2, 2, 2); other fields are ignored.  The workspace (device, 256-byte
+ * aligned, pcot_la_workspace_bytes; 0 bytes except for PCOT_COT) holds the
+ * queue and the counters.  The handle supplies the device status block (its
+ * coefficients are not used).  Asynchronous on `stream`; a dependency wait
+ * that times out is reported by pcot_check.
+ * ------------------------------------------------------------------------ */
+typedef enum { PCOT_LA_LU = 0, PCOT_LA_CHOLESKY = 1 } pcot_la_kind;
+
+pcot_status pcot_la_workspace_bytes(pcot_la_kind kind, int64_t n, pcot_schedule schedule,
+                                    const pcot_tile_params *params, size_t *bytes);
+pcot_status pcot_la_run(pcot_handle h, pcot_la_kind kind, void *A, void *workspace, size_t workspace_bytes,
+                        int64_t n, int64_t lda, pcot_dtype dtype, pcot_schedule schedule,
+                        const pcot_tile_params *params, void *stream);
+/*
+ * The tile plan without running it (host only, no GPU needed): *L tiles per
+ * side, *b the tile side, *n_tiles the number of non-empty tiles; queue
+ * (n_tiles ids (kb * L + ib) * L + jb in execution order: lexicographic for
+ * PCOT_SLT, recursive for PCOT_COT) and deps (L^3 entries: predecessors of
+ * each id in the tile graph) are filled up to cap entries when not NULL.
+ */
+pcot_status pcot_la_plan_query(pcot_la_kind kind, int64_t n, pcot_schedule schedule,
+                               const pcot_tile_params *params, int32_t *L, int32_t *b, int64_t *n_tiles,
+                               int32_t *queue, int32_t *deps, int64_t cap);
+
 /*
  * Number of kernels this handle has launched since it was created (sweep
  * steps, single-level blocks, persistent executors, ring copies, sums).

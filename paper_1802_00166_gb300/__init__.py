@@ -38,6 +38,10 @@ PCOT_COT = 2
 PCOT_AUTO = 3
 
 SCHEDULES = {"sweep": PCOT_SWEEP, "slt": PCOT_SLT, "cot": PCOT_COT, "auto": PCOT_AUTO}
+
+PCOT_LA_LU = 0
+PCOT_LA_CHOLESKY = 1
+LA_KINDS = {"lu": PCOT_LA_LU, "cholesky": PCOT_LA_CHOLESKY}
 DTYPES = {"f32": PCOT_F32, "f64": PCOT_F64, "f64_exact": PCOT_F64_EXACT}
 
 
@@ -126,6 +130,12 @@ def _load():
                                             ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
         "pcot_fdtd2d_run": (S, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64,
                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_la_workspace_bytes": (S, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
+                                        ctypes.POINTER(ctypes.c_size_t)]),
+        "pcot_la_run": (S, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
+        "pcot_la_plan_query": (S, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
+                                   _I32P, _I32P, _I64P, _I32P, _I32P, ctypes.c_int64]),
         "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
                           ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
@@ -142,6 +152,7 @@ def exported_symbols():
     """Names declared in include/pcot.h that this binding marshals."""
     return ["pcot_gs2d_workspace_bytes", "pcot_gs2d_run", "pcot_gs2d_plan_query",
             "pcot_fdtd2d_workspace_bytes", "pcot_fdtd2d_run",
+            "pcot_la_workspace_bytes", "pcot_la_run", "pcot_la_plan_query",
             "pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
             "pcot_run_host", "pcot_check", "pcot_plan_query", "pcot_test_wait_timeout", "pcot_grid_sum",
             "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
@@ -288,6 +299,40 @@ def pcot_fdtd2d_run(h, ex, ey, hz, fict, workspace, workspace_bytes, sizes, stri
     _chk(_load().pcot_fdtd2d_run(h, _ptr(ex), _ptr(ey), _ptr(hz), _ptr(fict), _ptr(workspace), int(workspace_bytes),
                                  _p64(s), _p64(st), int(T), int(dtype), int(schedule), _params(params),
                                  _stream(stream)), "pcot_fdtd2d_run")
+
+
+def pcot_la_workspace_bytes(kind, n, schedule, params=None):
+    b = ctypes.c_size_t()
+    _chk(_load().pcot_la_workspace_bytes(int(kind), int(n), int(schedule), _params(params), ctypes.byref(b)),
+         "pcot_la_workspace_bytes")
+    return int(b.value)
+
+
+def pcot_la_run(h, kind, A, workspace, workspace_bytes, n, lda, dtype, schedule, params=None, stream=None):
+    """LU or Cholesky of the n x n device matrix A (row stride lda), in place
+    (see include/pcot.h)."""
+    _chk(_load().pcot_la_run(h, int(kind), _ptr(A), _ptr(workspace), int(workspace_bytes), int(n), int(lda),
+                             int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_la_run")
+
+
+def pcot_la_plan_query(kind, n, schedule, params=None, with_queue=True):
+    lib = _load()
+    L = ctypes.c_int32()
+    b = ctypes.c_int32()
+    nt = ctypes.c_int64()
+    _chk(lib.pcot_la_plan_query(int(kind), int(n), int(schedule), _params(params), ctypes.byref(L), ctypes.byref(b),
+                                ctypes.byref(nt), None, None, 0), "pcot_la_plan_query")
+    out = dict(L=L.value, b=b.value, n_tiles=nt.value)
+    if with_queue:
+        ncell = L.value ** 3
+        cap = max(nt.value, ncell)
+        qq = np.zeros(cap, dtype=np.int32)
+        dd = np.zeros(cap, dtype=np.int32)
+        _chk(lib.pcot_la_plan_query(int(kind), int(n), int(schedule), _params(params), None, None, None,
+                                    qq.ctypes.data_as(_I32P), dd.ctypes.data_as(_I32P), cap), "pcot_la_plan_query")
+        out["queue"] = qq[:nt.value].copy()
+        out["deps"] = dd[:ncell].copy()
+    return out
 
 
 def pcot_run_host(h, host_grid, dev_grid, workspace, workspace_bytes, sizes, strides, T, dtype, schedule,

@@ -12,6 +12,7 @@
 
 #include "kernels.h"
 #include "pcot.h"
+#include "la_graph.h"
 #include "planner.h"
 
 using namespace pcot;
@@ -43,6 +44,13 @@ struct GsPlanCache {
     size_t image_bytes = 0, counts_bytes = 0;
 };
 
+// LU / Cholesky recursive plan with its upload image ([head block][counts][queue]).
+struct LaPlanCache {
+    LaPlanHost plan;
+    void* pinned = nullptr;
+    size_t image_bytes = 0, counts_bytes = 0;
+};
+
 // FDTD-2D recursive plan: queue and counters of the (block, tile) lattice.
 struct FdPlanCache {
     int32_t lattice[4] = {0, 1, 1, 1};
@@ -64,6 +72,7 @@ struct pcot_plan {
     std::map<std::string, CotPlanHost*> cot_cache;
     std::map<std::string, GsPlanCache*> gs_cache;
     std::map<std::string, FdPlanCache*> fd_cache;
+    std::map<std::string, LaPlanCache*> la_cache;
     uint64_t timeout_ns = kDefaultTimeoutNs;
     int64_t launches = 0;  // kernels launched by this handle
 };
@@ -402,6 +411,10 @@ pcot_status pcot_destroy(pcot_handle h) {
         delete kv.second;
     }
     for (auto& kv : h->fd_cache) {
+        if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+        delete kv.second;
+    }
+    for (auto& kv : h->la_cache) {
         if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
         delete kv.second;
     }
@@ -1355,6 +1368,149 @@ pcot_status pcot_fdtd2d_run(pcot_handle h, void* ex, void* ey, void* hz, const v
     if (cur) {  // the result is in the workspace copy
         for (int a = 0; a < 3; ++a) PCOT_CUDA(cudaMemcpyAsync(f0[a], f1[a], span, cudaMemcpyDeviceToDevice, s));
     }
+    return PCOT_OK;
+}
+
+}  // extern "C"
+
+// ---- LU / Cholesky ------------------------------------------------------------
+namespace {
+
+bool la_shape(pcot_la_kind kind, pcot_schedule schedule, const pcot_tile_params* p, int32_t* b, int32_t* theta) {
+    if (kind != PCOT_LA_LU && kind != PCOT_LA_CHOLESKY) return false;
+    if (schedule != PCOT_SWEEP && schedule != PCOT_SLT && schedule != PCOT_COT) return false;
+    *b = (p && p->tile[0] > 0) ? p->tile[0] : 64;
+    for (int d = 0; d < 3; ++d) theta[d] = (p && p->cot_threshold[d] > 0) ? p->cot_threshold[d] : 2;
+    return la_block_supported(*b);
+}
+
+pcot_status la_get_plan(pcot_handle h, pcot_la_kind kind, int64_t n, pcot_schedule schedule, int32_t b,
+                        const int32_t* theta, LaPlanCache** out) {
+    char key[128];
+    snprintf(key, sizeof(key), "%d,%lld,%d,%d,%d,%d,%d", (int)kind, (long long)n, (int)schedule, b, theta[0], theta[1],
+             theta[2]);
+    if (h) {
+        auto it = h->la_cache.find(key);
+        if (it != h->la_cache.end()) {
+            *out = it->second;
+            return PCOT_OK;
+        }
+    }
+    LaPlanCache* c = new LaPlanCache();
+    if (!la_plan((int)kind, n, b, schedule == PCOT_COT ? 1 : 0, theta, &c->plan)) {
+        delete c;
+        return PCOT_ERR_UNSUPPORTED;
+    }
+    c->counts_bytes = round_up(c->plan.deps.size() * 4, kAlign);
+    c->image_bytes = kAlign + c->counts_bytes + round_up(c->plan.queue.size() * 4 + 4, kAlign);
+    if (h) {
+        if (h->la_cache.size() >= 16) {
+            for (auto& kv : h->la_cache) {
+                if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+                delete kv.second;
+            }
+            h->la_cache.clear();
+        }
+        h->la_cache[key] = c;
+    }
+    *out = c;
+    return PCOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcot_status pcot_la_plan_query(pcot_la_kind kind, int64_t n, pcot_schedule schedule, const pcot_tile_params* params,
+                               int32_t* L, int32_t* b, int64_t* n_tiles, int32_t* queue, int32_t* deps, int64_t cap) {
+    if (n < 1 || n > (1LL << 30)) return PCOT_ERR_INVALID_ARG;
+    int32_t bb = 0, th[3];
+    if (!la_shape(kind, schedule, params, &bb, th)) return PCOT_ERR_UNSUPPORTED;
+    LaPlanCache* c = nullptr;
+    PCOT_TRY(la_get_plan(nullptr, kind, n, schedule, bb, th, &c));
+    if (L) *L = c->plan.L;
+    if (b) *b = bb;
+    if (n_tiles) *n_tiles = (int64_t)c->plan.queue.size();
+    if (queue)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.queue.size(); ++k) queue[k] = c->plan.queue[(size_t)k];
+    if (deps)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.deps.size(); ++k) deps[k] = c->plan.deps[(size_t)k];
+    delete c;
+    return PCOT_OK;
+}
+
+pcot_status pcot_la_workspace_bytes(pcot_la_kind kind, int64_t n, pcot_schedule schedule,
+                                    const pcot_tile_params* params, size_t* bytes) {
+    if (!bytes || n < 0 || n > (1LL << 30)) return PCOT_ERR_INVALID_ARG;
+    int32_t b = 0, th[3];
+    if (!la_shape(kind, schedule, params, &b, th)) return PCOT_ERR_UNSUPPORTED;
+    *bytes = 0;
+    if (schedule != PCOT_COT || n == 0) return PCOT_OK;
+    const int64_t L = (n + b - 1) / b;
+    if (L > 256) return PCOT_ERR_UNSUPPORTED;
+    // head block + counts of every lattice id + the queue (at most every id)
+    *bytes = kAlign + round_up((size_t)(L * L * L) * 4, kAlign) + round_up((size_t)(L * L * L) * 4 + 4, kAlign);
+    return PCOT_OK;
+}
+
+pcot_status pcot_la_run(pcot_handle h, pcot_la_kind kind, void* A, void* workspace, size_t workspace_bytes, int64_t n,
+                        int64_t lda, pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
+                        void* stream) {
+    if (!h || n < 0 || n > (1LL << 30) || lda < n || (n > 0 && !A)) return PCOT_ERR_INVALID_ARG;
+    if (dtype != PCOT_F32 && dtype != PCOT_F64 && dtype != PCOT_F64_EXACT) return PCOT_ERR_INVALID_ARG;
+    if (dtype == PCOT_F32) return PCOT_ERR_UNSUPPORTED;
+    int32_t b = 0, th[3];
+    if (!la_shape(kind, schedule, params, &b, th)) return PCOT_ERR_UNSUPPORTED;
+    if (((uintptr_t)A % 8) != 0) return PCOT_ERR_ALIGNMENT;
+    if (n == 0) return PCOT_OK;
+    size_t need = 0;
+    PCOT_TRY(pcot_la_workspace_bytes(kind, n, schedule, params, &need));
+    if (need && (!workspace || workspace_bytes < need)) return PCOT_ERR_OOM;
+    if (need && ((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
+    PCOT_TRY(ensure_device(h));
+    cudaStream_t s = (cudaStream_t)stream;
+    LaDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.A = (double*)A;
+    d.lda = lda;
+    d.n = n;
+    d.b = b;
+    d.L = (int32_t)((n + b - 1) / b);
+    d.status = h->d_status;
+    d.timeout_ns = h->timeout_ns;
+    const bool fused = dtype == PCOT_F64;
+    const int k = kind == PCOT_LA_LU ? kLaLU : kLaCholesky;
+    int nctas = 0;
+    if (schedule == PCOT_COT) {
+        LaPlanCache* c = nullptr;
+        PCOT_TRY(la_get_plan(h, kind, n, schedule, b, th, &c));
+        if (c->plan.queue.empty()) return PCOT_OK;  // LU of a 1 x 1 matrix: nothing to do
+        if (!c->pinned) {
+            void* p = nullptr;
+            PCOT_CUDA(cudaMallocHost(&p, c->image_bytes));
+            unsigned char* img = (unsigned char*)p;
+            std::memset(img, 0, c->image_bytes);
+            std::memcpy(img + kAlign, c->plan.deps.data(), c->plan.deps.size() * 4);
+            std::memcpy(img + kAlign + c->counts_bytes, c->plan.queue.data(), c->plan.queue.size() * 4);
+            c->pinned = p;
+        }
+        unsigned char* ws = (unsigned char*)workspace;
+        PCOT_CUDA(cudaMemcpyAsync(ws, c->pinned, c->image_bytes, cudaMemcpyHostToDevice, s));
+        d.head = (int32_t*)ws;
+        d.counts = (int32_t*)(ws + kAlign);
+        d.queue = (const int32_t*)(ws + kAlign + c->counts_bytes);
+        d.ntiles = (int64_t)c->plan.queue.size();
+        const int per_sm = la_ctas_per_sm(b, fused, k);
+        if (per_sm < 1) return PCOT_ERR_UNSUPPORTED;
+        int64_t m = (int64_t)per_sm * h->num_sms;
+        if (m > d.ntiles) m = d.ntiles;
+        nctas = (int)m;
+    }
+    int64_t launches = 0;
+    const cudaError_t e = launch_la(d, k, fused, schedule == PCOT_SWEEP ? kLaSweep : schedule == PCOT_SLT ? kLaSlt : kLaCot,
+                                    nctas, s, &launches);
+    h->launches += launches;
+    PCOT_CUDA(e);
     return PCOT_OK;
 }
 

@@ -51,4 +51,16 @@ struct GsPlanHost {
 bool gs_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
              GsPlanHost* out);
 
+// LU / Cholesky tile plan (planner_la.cpp): the non-empty tiles
+// (kb * L + ib) * L + jb of the b x b x b lattice over the (k, i, j) space in
+// execution order (lexicographic, or the recursive order when `recursive`),
+// and per lattice id its number of predecessors in the tile graph of
+// la_graph.h.
+struct LaPlanHost {
+    int32_t L = 0;
+    std::vector<int32_t> queue;
+    std::vector<int32_t> deps;
+};
+bool la_plan(int kind, int64_t n, int32_t b, int recursive, const int32_t* theta, LaPlanHost* out);
+
 }  // namespace pcot

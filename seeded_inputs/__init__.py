@@ -136,3 +136,17 @@ def random_coefficients(dims: int, radius: int, seed: int) -> np.ndarray:
     """Distinct coefficients in [-1, 1) (tests of operand order and signs)."""
     k = 1 + 2 * dims * radius
     return 2.0 * uniform01(seed, k) - 1.0
+
+
+def dominant_matrix(n: int, seed: int, symmetric: bool = False) -> np.ndarray:
+    """n x n FP64 matrix with off-diagonal entries U[0, 1) and diagonal
+    entries n + U[0, 1): strictly diagonally dominant, so elimination without
+    pivoting is stable; with ``symmetric`` the strict lower triangle's draws
+    are mirrored above the diagonal (then the matrix is also positive
+    definite, by Gershgorin's theorem).  Draws in row-major order."""
+    a = uniform01(seed, n * n).reshape(n, n).copy()
+    if symmetric:
+        lower = np.tril(a, -1)
+        a = lower + lower.T + np.diag(np.diag(a))
+    a[np.diag_indices(n)] += float(n)
+    return a
