@@ -439,7 +439,7 @@ def run_gpu(args):
                                 "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
     if args.schedules and rank == 0:
         line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
-    if (args.batched or args.gs2d or args.fdtd2d) and rank == 0:
+    if (args.batched or args.gs2d or args.fdtd2d or args.la) and rank == 0:
         del base, wsbuf, host
         torch.cuda.empty_cache()
     if args.batched and rank == 0:
@@ -448,6 +448,8 @@ def run_gpu(args):
         line["gs2d"] = run_gs2d(pcot, h, stream, args.steps)
     if args.fdtd2d and rank == 0:
         line["fdtd2d"] = run_fdtd2d(pcot, h, stream, args.steps)
+    if args.la and rank == 0:
+        line["la"] = run_la(pcot, h, stream, args.steps)
     pcot.pcot_destroy(h)
     if rank == 0:
         print(json.dumps(line))
@@ -568,6 +570,79 @@ def run_fdtd2d(pcot, h, stream, steps):
     return out
 
 
+LA = {"lu": {"n": 3000, "slt": {"tile": (32, 0, 0)}, "cot": {"tile": (32, 0, 0), "cot_threshold": (2, 32, 32)}},
+      "cholesky": {"n": 4000, "slt": {"tile": (32, 0, 0)},
+                   "cot": {"tile": (32, 0, 0), "cot_threshold": (2, 32, 32)}}}
+LA_CPU_SAMPLE_N = 1000
+
+
+def run_la(pcot, h, stream, steps):
+    """LU (no pivoting) and Cholesky at the paper's sizes (Table 2: LUD 3000^2,
+    Cholesky 4000^2), FP64, seeded diagonally dominant matrices resident on
+    the device, factored in place under the sweep, level-synchronous and
+    recursive-order schedules, fused (PCOT_F64) and unfused (PCOT_F64_EXACT)
+    updates, each bitwise the oracle's loops.  CUDA events around each
+    factorization (the copy that restores the input is outside them).  Roof:
+    the DP pipe, against the part's nominal 1.25 TFLOP/s (LU 2n^3/3 flops,
+    Cholesky n^3/3); the unfused mode issues two DP instructions per update,
+    so it tops out at half that rate."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import seeded_inputs as si
+    out = {"unit": "GFLOP/s", "flops": "LU 2n^3/3, Cholesky n^3/3",
+           "inputs": "seeded, off-diagonal U[0,1), diagonal n + U[0,1) (Cholesky: symmetric)"}
+    for kind in ("lu", "cholesky"):
+        n = LA[kind]["n"]
+        K = pcot.LA_KINDS[kind]
+        A0 = torch.from_numpy(si.dominant_matrix(n, 7, symmetric=(kind == "cholesky"))).cuda()
+        A = torch.empty_like(A0)
+        flops = 2.0 * n ** 3 / 3 if kind == "lu" else n ** 3 / 3.0
+        res = {"workload": f"{kind} {n}x{n} fp64 in place"}
+        for dtype, dn in ((pcot.PCOT_F64, "f64"), (pcot.PCOT_F64_EXACT, "f64_exact")):
+            for name, sched, prm in (("sweep", pcot.PCOT_SWEEP, None), ("slt", pcot.PCOT_SLT, LA[kind]["slt"]),
+                                     ("cot", pcot.PCOT_COT, LA[kind]["cot"])):
+                p = pcot.tile_params(**prm) if prm else None
+                nb = pcot.pcot_la_workspace_bytes(K, n, sched, p)
+                ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+                reps = max(2, min(steps, 4))
+                total = 0.0
+                for r in range(reps + 1):
+                    A.copy_(A0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    pcot.pcot_la_run(h, K, A.data_ptr(), ws.data_ptr(), nb, n, n, dtype, sched, p, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if r > 0:  # the first run is the warm-up
+                        total += e0.elapsed_time(e1)
+                st = pcot.pcot_check(h, stream)
+                if st != pcot.PCOT_OK:
+                    raise pcot.PcotError(st, f"{kind} {name}")
+                ms = total / reps
+                gf = flops / ms / 1e6
+                res[f"{name}_{dn}"] = {"ms": ms, "GFLOP/s": gf,
+                                       "roofline": {"bound": "alu", "achieved": gf, "peak": 1250.0,
+                                                    "unit": "GFLOP/s", "frac": gf / 1250.0, "peak_kind": "nominal"},
+                                       "params": {a: list(v) if isinstance(v, tuple) else v
+                                                  for a, v in (prm or {}).items()}}
+        # the oracle (one core) on a bounded sample of the same kind of matrix
+        m = LA_CPU_SAMPLE_N
+        As = si.dominant_matrix(m, 7, symmetric=(kind == "cholesky"))
+        t0 = time.perf_counter()
+        getattr(oracle, kind)(As, fused=False)
+        dt = time.perf_counter() - t0
+        fs = 2.0 * m ** 3 / 3 if kind == "lu" else m ** 3 / 3.0
+        res["cpu_baseline"] = {"value": fs / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{kind} of a {m}x{m} matrix (plain loops, unfused)"}
+        out[kind] = res
+        del A, A0
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(pcot, stream, steps):
     """256 independent Heat-2D grids (sides log-uniform in [256, 2048], T in
     [64, 1024], seeded) advanced by one persistent launch replayed from a CUDA
@@ -679,6 +754,26 @@ def run_profile_case(args):
     n, T = args.case_n, args.case_T
     th = tuple(int(v) for v in args.case_theta.split(","))
     sched = pcot.SCHEDULES[args.profile_case]
+    if args.case_la:
+        # LU / Cholesky of a seeded n x n FP64 matrix (tile side from --case-tile)
+        import seeded_inputs as si
+        kind = pcot.LA_KINDS[args.case_la]
+        b = int(args.case_tile.split(",")[0])
+        h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+        A0 = torch.from_numpy(si.dominant_matrix(n, 7, symmetric=(args.case_la == "cholesky"))).cuda()
+        A = torch.empty_like(A0)
+        p = pcot.tile_params(tile=(b, 0, 0), cot_threshold=th)
+        nb = pcot.pcot_la_workspace_bytes(kind, n, sched, p)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        for _ in range(args.case_runs):
+            A.copy_(A0)
+            pcot.pcot_la_run(h, kind, A.data_ptr(), ws.data_ptr(), nb, n, n, pcot.PCOT_F64, sched, p)
+        st = pcot.pcot_check(h)
+        pcot.pcot_destroy(h)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "profile case")
+        print(f"ok {args.case_la} {args.profile_case} n={n} b={b} theta={th}")
+        return 0
     if args.case_dims == 3:
         # Jacobi-3D 7-point, periodic n^3 grid (the 3-D workload's stencil)
         tile = tuple(int(v) for v in args.case_tile.split(","))
@@ -724,9 +819,12 @@ def main():
     ap.add_argument("--batched", action="store_true", help="also time the 256-grid batched persistent launch")
     ap.add_argument("--gs2d", action="store_true", help="also time Gauss-Seidel 2-D at the paper's size")
     ap.add_argument("--fdtd2d", action="store_true", help="also time FDTD-2D at the paper's size")
+    ap.add_argument("--la", action="store_true", help="also time LU and Cholesky at the paper's sizes")
     ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
     ap.add_argument("--case-dims", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--case-la", default=None, choices=[None, "lu", "cholesky"],
+                    help="profile case: an LU or Cholesky factorization instead of a stencil")
     ap.add_argument("--case-n", type=int, default=8192)
     ap.add_argument("--case-T", type=int, default=64)
     ap.add_argument("--case-k", type=int, default=8)

@@ -459,9 +459,9 @@ pcot_status pcot_fdtd2d_run(pcot_handle h, void *ex, void *ey, void *hz, const v
  * PCOT_COT the same tiles in the recursive order over the tile lattice
  * (orthants with equal numbers of upper halves side by side, leaves
  * lexicographic), run by a persistent kernel that waits (bounded) on
- * per-tile dependency counters.  params: tile[0] = b (32 or 64, default 64),
+ * per-tile dependency counters.  params: tile[0] = b (32 or 64, default 32),
  * cot_threshold[0..2] = recursion leaf in tiles along (k, i, j) (default
- * 2, 2, 2); other fields are ignored.  The workspace (device, 256-byte
+ * 2, 32, 32); other fields are ignored.  The workspace (device, 256-byte
  * aligned, pcot_la_workspace_bytes; 0 bytes except for PCOT_COT) holds the
  * queue and the counters.  The handle supplies the device status block (its
  * coefficients are not used).  Asynchronous on `stream`; a dependency wait

@@ -104,6 +104,28 @@ int cot_ctas_per_sm(const LaunchCtx& L, const TileGeo& t);
 // Dynamic shared memory of one CTA for this geometry.
 size_t tile_smem_bytes(const LaunchCtx& L, const TileGeo& t);
 
+// ---- k_la.cu: blocked LU / Cholesky (tile graph in la_graph.h) ----
+enum { kLaSweep = 0, kLaSlt = 1, kLaCot = 2 };
+struct LaDev {
+    double* A;             // n x n, row stride lda, factored in place
+    int64_t lda, n;
+    int32_t b;             // tile side (32 or 64)
+    int32_t L;             // tiles per side, ceil(n / b)
+    const int32_t* queue;  // recursive schedule: non-empty tile ids in execution order
+    int32_t* counts;       // remaining predecessors per tile id (L^3)
+    int32_t* head;         // next queue position to pop
+    int64_t ntiles;
+    DevStatus* status;
+    uint64_t timeout_ns;
+};
+bool la_block_supported(int b);
+// Resident CTAs per SM of the persistent kernel.
+int la_ctas_per_sm(int b, bool fused, int kind);
+// Runs the schedule (kLaSweep / kLaSlt / kLaCot) on `s`; *launches counts the
+// kernel launches issued.
+cudaError_t launch_la(const LaDev& d, int kind, bool fused, int schedule, int nctas, cudaStream_t s,
+                      int64_t* launches);
+
 // ---- k_mlp.cu ----
 namespace mlp {
 int param_count();
