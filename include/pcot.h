@@ -454,8 +454,10 @@ pcot_status pcot_fdtd2d_run(pcot_handle h, void *ex, void *ey, void *hz, const v
  * each update one fused multiply-add, PCOT_F64_EXACT with a rounded product
  * and a rounded difference.  PCOT_F32 is not supported.
  * Schedules: PCOT_SWEEP the plain loop over k (two launches per k);
- * PCOT_SLT tiles of b x b x b points of the (k, i, j) space, one launch each
- * for the diagonal tile, the panels and the updates of every block step;
+ * PCOT_SLT tiles of b x b x b points of the (k, i, j) space, block step by
+ * block step: a launch for the panels and one for the updates (the next
+ * step's diagonal tile is factored inside the update launch, by the CTA that
+ * updates that block);
  * PCOT_COT the same tiles in the recursive order over the tile lattice
  * (orthants with equal numbers of upper halves side by side, leaves
  * lexicographic), run by a persistent kernel that waits (bounded) on

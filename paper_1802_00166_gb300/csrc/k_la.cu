@@ -4,8 +4,9 @@
 //  * sweep: the plain loop over k, two launches per k (the column of
 //    multipliers, then the trailing update), one thread per element;
 //  * single-level: b x b x b tiles of the (k, i, j) space, block step kb by
-//    block step: one launch for the diagonal tile, one for the panels, one for
-//    the updates (tiles of one launch are independent);
+//    block step: one launch for the panels and one for the updates (tiles of
+//    one launch are independent); the diagonal tile of step kb+1 is factored
+//    inside step kb's update launch by the CTA that updates that block last;
 //  * recursive: the same tiles in the recursive order of planner_la.cpp, run
 //    by a persistent kernel that pops the queue in order, waits (bounded) on
 //    per-tile dependency counters and releases the successors of la_graph.h.
@@ -270,7 +271,11 @@ __global__ void __launch_bounds__(kLaThreads) la_cot_kernel(LaDev d) {
 }
 
 // One launch of the single-level schedule: phase 0 the diagonal tile of
-// block step kb, phase 1 its panels, phase 2 its updates.
+// block step kb, phase 1 its panels, phase 2 its updates.  In phase 2 the
+// CTA of the first update tile, (kb, kb+1, kb+1), goes on to factor that
+// block as the diagonal tile of step kb+1 (it depends on nothing else), so
+// the next step needs no launch of its own for it and the factorization
+// overlaps the rest of this step's updates.
 template <int B, bool FUSED, int KIND>
 __global__ void __launch_bounds__(kLaThreads) la_step_kernel(LaDev d, int kb, int phase) {
     extern __shared__ __align__(16) unsigned char la_smraw[];
@@ -298,6 +303,10 @@ __global__ void __launch_bounds__(kLaThreads) la_step_kernel(LaDev d, int kb, in
     }
     if (!la_tile_nonempty(KIND, d.n, B, L, kb, ib, jb)) return;
     run_tile<B, FUSED, KIND>(d, sm, kb, ib, jb);
+    // run_tile ends with a CTA barrier, so this CTA's stores of the block are
+    // visible to its own loads of it below
+    if (phase == 2 && x == 0 && la_tile_nonempty(KIND, d.n, B, L, kb + 1, kb + 1, kb + 1))
+        run_tile<B, FUSED, KIND>(d, sm, kb + 1, kb + 1, kb + 1);
 }
 
 // ---- the plain loop over k ------------------------------------------------
@@ -349,14 +358,17 @@ cudaError_t la_launch_t(const LaDev& d, int schedule, int nctas, cudaStream_t s,
         cudaError_t e = cudaFuncSetAttribute(la_step_kernel<B, FUSED, KIND>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
+        bool diag_done = false;  // factored by the previous step's update launch
         for (int64_t kb = 0; kb < d.L; ++kb) {
             const int64_t m = d.L - 1 - kb;
-            const int64_t counts[3] = {1, KIND == kLaLU ? 2 * m : m, KIND == kLaLU ? m * m : m * (m + 1) / 2};
+            const int64_t counts[3] = {diag_done ? 0 : 1, KIND == kLaLU ? 2 * m : m,
+                                       KIND == kLaLU ? m * m : m * (m + 1) / 2};
             for (int ph = 0; ph < 3; ++ph) {
                 if (counts[ph] == 0) continue;
                 la_step_kernel<B, FUSED, KIND><<<(unsigned)counts[ph], kLaThreads, sm, s>>>(d, (int)kb, ph);
                 ++*launches;
             }
+            diag_done = counts[2] > 0;
         }
         return cudaGetLastError();
     }

@@ -107,8 +107,8 @@ def test_upper_triangle_untouched_by_cholesky_and_sweeps_agree(handle, kind):
 
 
 def test_launch_counts(handle):
-    """Sweep: two launches per k; single-level: three per block step (fewer
-    at the end); recursive: one persistent launch."""
+    """Sweep: two launches per k; single-level: panels and updates per block
+    step (plus the first diagonal tile); recursive: one persistent launch."""
     n = 130
     A = matrix("lu", n, 5)
     c0 = pcot.pcot_launch_count(handle)
@@ -117,7 +117,8 @@ def test_launch_counts(handle):
     assert c1 - c0 == 1
     run_la(handle, "lu", A, pcot.PCOT_F64, pcot.PCOT_SLT, dict(tile=(64, 0, 0)))
     c2 = pcot.pcot_launch_count(handle)
-    assert c2 - c1 == 3 + 3 + 1  # L = 3: two full block steps and the last diagonal tile
+    assert c2 - c1 == 3 + 2  # L = 3: diagonal, panels, updates; then panels, updates (the next
+    # diagonal tiles are factored inside the update launches)
     run_la(handle, "lu", A, pcot.PCOT_F64, pcot.PCOT_SWEEP)
     c3 = pcot.pcot_launch_count(handle)
     assert c3 - c2 == 2 * (n - 1)
