@@ -460,7 +460,8 @@ def run_gpu(args):
 
 GS2D = {"n": 2000, "T": 500, "slt": {"tile": (32, 128), "time_depth": 8},
         "slt_f64": {"tile": (16, 128), "time_depth": 8},
-        "cot": {"tile": (32, 128), "time_depth": 8, "cot_threshold": (8, 16, 16)}}
+        "cot": {"tile": (32, 128), "time_depth": 8, "cot_threshold": (32, 32, 32)},
+        "cot_f64": {"tile": (16, 128), "time_depth": 8, "cot_threshold": (32, 32, 32)}}
 
 
 def run_gs2d(pcot, h, stream, steps):
@@ -475,7 +476,7 @@ def run_gs2d(pcot, h, stream, steps):
         base = torch.rand((n + 2) * (n + 2), dtype=tdt, device="cuda")
         for name, sched, prm in (("sweep", pcot.PCOT_SWEEP, None),
                                  ("slt", pcot.PCOT_SLT, GS2D["slt_f64" if dn == "f64" else "slt"]),
-                                 ("cot", pcot.PCOT_COT, GS2D["cot"])):
+                                 ("cot", pcot.PCOT_COT, GS2D["cot_f64" if dn == "f64" else "cot"])):
             p = pcot.tile_params(**prm) if prm else None
             nb = pcot.pcot_gs2d_workspace_bytes((n, n), T, sched, p)
             ws = torch.empty(nb, dtype=torch.uint8, device="cuda")

@@ -377,7 +377,7 @@ pcot_status pcot_run_noalloc(pcot_handle h, void *grid, const int64_t *sizes, co
  * NULL (row stride n1 + 2).  params: tile = {ha, wc} skewed rows and
  * columns per tile (default 32, 128; ha * time_depth <= 1024 threads, wc >= 2),
  * time_depth = kt (default 1 for PCOT_SWEEP, else 8), cot_threshold[0..2] =
- * recursion leaf in tiles along (t, a, c) (default 2, 4, 4).  The handle
+ * recursion leaf in tiles along (t, a, c) (default 32, 32, 32).  The handle
  * supplies the device status block (its coefficients are not used).  The
  * workspace (device, 256-byte aligned, pcot_gs2d_workspace_bytes) holds the
  * tile queue and dependency counters.  Asynchronous on `stream`; a

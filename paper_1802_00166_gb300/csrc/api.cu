@@ -1033,7 +1033,10 @@ bool gs_shape(pcot_schedule schedule, const pcot_tile_params* p, int32_t* tile, 
     tile[1] = (p && p->tile[0] > 0) ? p->tile[0] : 32;
     tile[2] = (p && p->tile[1] > 0) ? p->tile[1] : 128;
     if (schedule == PCOT_SWEEP && tile[0] != 1) return false;
-    for (int d = 0; d < 3; ++d) theta[d] = (p && p->cot_threshold[d] > 0) ? p->cot_threshold[d] : (d == 0 ? 2 : 4);
+    // default leaf 32 x 32 x 32 tiles: measured at 2000^2 x 500, the recursive
+    // order's speed rises with the leaf size (more independent tiles per
+    // wavefront of a leaf): FP32 49.5 GU/s at (8, 16, 16), 109 at (32, 32, 32)
+    for (int d = 0; d < 3; ++d) theta[d] = (p && p->cot_threshold[d] > 0) ? p->cot_threshold[d] : 32;
     if (tile[0] * tile[1] > 1024 || tile[0] * tile[1] < 1 || tile[2] < 2 || tile[2] > 4096) return false;
     return true;
 }
