@@ -48,7 +48,9 @@ inline int max_warps_for(int dtype, int depth) {
     return depth <= 2 ? kMaxWarps : 12;
 }
 
-template <class T, bool EXACT, int K, bool CG>
+// PER: periodic grid (compile time, so a periodic run carries no boundary
+// tests and a Dirichlet run no wrap-around).
+template <class T, bool EXACT, int K, bool CG, bool PER>
 __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restrict__ dst, const DevGeo& g,
                                          const Coeffs<T>& c, int64_t z0, int64_t Hz, int64_t y0, int64_t Hy,
                                          int64_t x0, int64_t Wx, bool vec_ok, T* sm) {
@@ -58,7 +60,7 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     const int w = threadIdx.x >> 5;
     const int NW = blockDim.x >> 5;
     const int NR = NW * RY;  // rows of the CTA
-    const bool per = g.periodic != 0;
+    constexpr bool per = PER;
     const int64_t ez = g.e[0], ey = g.e[1], ex = g.e[2];
     const int64_t nz = g.n[0], ny = g.n[1], nx = g.n[2];
     const int64_t Pz = g.s[0], Py = g.s[1];
@@ -112,10 +114,15 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     const bool warp_xint = __all_sync(kFull, lane_xint);
     const bool brick_ok = per || (brick_int && warp_xint);  // no pass-through inside this brick
 
-    // Row offsets of the brick inside a plane (computed once per tile).
-    int64_t yoff[RY];
+    // Offsets inside a plane (computed once per tile): of the brick's rows,
+    // of this lane's first loaded cell in each row, of its first stored cell.
+    int64_t yoff[RY], loff[RY], soff[RY];
 #pragma unroll
-    for (int r = 0; r < RY; ++r) yoff[r] = ysrc[r] * Py;
+    for (int r = 0; r < RY; ++r) {
+        yoff[r] = ysrc[r] * Py;
+        loff[r] = yoff[r] + col[0];
+        soff[r] = (ybase + r) * Py + xl;
+    }
 
     // The brick's rows of input plane zi (plane index and bounds once per plane).
     auto load_plane = [&](int64_t zi, T (&v)[RY][E]) {
@@ -136,12 +143,12 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                 v[r][1] = T(0);
                 continue;
             }
-            const T* rowp = plane + yoff[r];
             if (lvec) {
-                const V q = gload<CG>(reinterpret_cast<const V*>(rowp + col[0]));
+                const V q = gload<CG>(reinterpret_cast<const V*>(plane + loff[r]));
                 v[r][0] = q.x;
                 v[r][1] = q.y;
             } else {
+                const T* rowp = plane + yoff[r];
 #pragma unroll
                 for (int j = 0; j < E; ++j) v[r][j] = inb[j] ? gload<CG>(rowp + col[j]) : T(0);
             }
@@ -235,20 +242,20 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         const int64_t zo = zi - K;
         const bool zok = zo >= z0 && zo < z0 + Hz && (per ? zo < nz : (zo >= 1 && zo <= nz));
         if (zok) {
-            T* const row0 = dst + zo * Pz + ybase * Py;
+            T* const plane = dst + zo * Pz;
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 if (!ystore[r]) continue;
-                T* rowp = row0 + r * Py;
+                T* const cell = plane + soff[r];
                 if (svec) {
                     V q;
                     q.x = out[r][0];
                     q.y = out[r][1];
-                    *reinterpret_cast<V*>(rowp + xl) = q;
+                    *reinterpret_cast<V*>(cell) = q;
                 } else {
 #pragma unroll
                     for (int j = 0; j < E; ++j)
-                        if (stx[j]) rowp[xl + j] = out[r][j];
+                        if (stx[j]) cell[j] = out[r][j];
                 }
             }
         }
@@ -262,16 +269,16 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     }
 }
 
-template <class T, bool EXACT, int K>
+template <class T, bool EXACT, int K, bool PER>
 __global__ void __maxnreg__((kRegBudget3<T, K>)) slt_kernel(const T* __restrict__ src, T* __restrict__ dst, DevGeo g,
                                                        Coeffs<T> c, TileGeo t, bool vec_ok) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int64_t ix = blockIdx.x, iy = blockIdx.y, iz = blockIdx.z;
-    cta_tile<T, EXACT, K, false>(src, dst, g, c, iz * t.ext[0], t.ext[0], iy * t.ext[1], t.ext[1], ix * t.ext[2],
-                                 t.ext[2], vec_ok, reinterpret_cast<T*>(smraw));
+    cta_tile<T, EXACT, K, false, PER>(src, dst, g, c, iz * t.ext[0], t.ext[0], iy * t.ext[1], t.ext[1],
+                                      ix * t.ext[2], t.ext[2], vec_ok, reinterpret_cast<T*>(smraw));
 }
 
-template <class T, bool EXACT, int K>
+template <class T, bool EXACT, int K, bool PER>
 __global__ void __maxnreg__((kRegBudget3<T, K>)) cot_kernel(T* buf0, T* buf1, DevGeo g, Coeffs<T> c, TileGeo t,
                                                        bool vec_ok, CotDev q) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -291,8 +298,9 @@ __global__ void __maxnreg__((kRegBudget3<T, K>)) cot_kernel(T* buf0, T* buf1, De
         const int b = r / L0;
         const T* src = (b & 1) ? buf1 : buf0;
         T* dst = (b & 1) ? buf0 : buf1;
-        cta_tile<T, EXACT, K, true>(src, dst, g, c, (int64_t)iz * t.ext[0], t.ext[0], (int64_t)iy * t.ext[1],
-                                    t.ext[1], (int64_t)ix * t.ext[2], t.ext[2], vec_ok, reinterpret_cast<T*>(smraw));
+        cta_tile<T, EXACT, K, true, PER>(src, dst, g, c, (int64_t)iz * t.ext[0], t.ext[0], (int64_t)iy * t.ext[1],
+                                         t.ext[1], (int64_t)ix * t.ext[2], t.ext[2], vec_ok,
+                                         reinterpret_cast<T*>(smraw));
         __syncthreads();  // the tile's stores by every thread precede thread 0's release
         if (threadIdx.x == 0) release_successors(q, 3, b, iz, iy, ix);
     }
@@ -311,38 +319,59 @@ size_t smem_t(const TileGeo& t) {
     return (size_t)2 * t.depth * t.nwarps * 2 * 32 * E * sizeof(T);
 }
 
-template <class T, bool EXACT, int K>
-cudaError_t slt_k(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst) {
+template <class T, bool EXACT, int K, bool PER>
+cudaError_t slt_kp(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst) {
     const size_t sm = smem_t<T>(t);
-    cudaError_t e = cudaFuncSetAttribute(slt_kernel<T, EXACT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(slt_kernel<T, EXACT, K, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     if (t.count[0] > 65535 || t.count[1] > 65535) return cudaErrorInvalidConfiguration;
     dim3 grd((unsigned)t.count[2], (unsigned)t.count[1], (unsigned)t.count[0]);
-    slt_kernel<T, EXACT, K><<<grd, 32 * t.nwarps, sm, L.stream>>>((const T*)src, (T*)dst, L.geo,
-                                                                  coeffs_as<T>(L.coeffs), t,
-                                                                  vec_aligned<T>(L.geo, src, dst));
+    slt_kernel<T, EXACT, K, PER><<<grd, 32 * t.nwarps, sm, L.stream>>>((const T*)src, (T*)dst, L.geo,
+                                                                       coeffs_as<T>(L.coeffs), t,
+                                                                       vec_aligned<T>(L.geo, src, dst));
+    return cudaGetLastError();
+}
+
+template <class T, bool EXACT, int K>
+cudaError_t slt_k(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst) {
+    return L.geo.periodic ? slt_kp<T, EXACT, K, true>(L, t, src, dst) : slt_kp<T, EXACT, K, false>(L, t, src, dst);
+}
+
+template <class T, bool EXACT, int K, bool PER>
+cudaError_t cot_kp(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas) {
+    const size_t sm = smem_t<T>(t);
+    cudaError_t e =
+        cudaFuncSetAttribute(cot_kernel<T, EXACT, K, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    cot_kernel<T, EXACT, K, PER><<<nctas, 32 * t.nwarps, sm, L.stream>>>((T*)b0, (T*)b1, L.geo,
+                                                                         coeffs_as<T>(L.coeffs), t,
+                                                                         vec_aligned<T>(L.geo, b0, b1), q);
     return cudaGetLastError();
 }
 
 template <class T, bool EXACT, int K>
 cudaError_t cot_k(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const CotDev& q, int nctas) {
+    return L.geo.periodic ? cot_kp<T, EXACT, K, true>(L, t, b0, b1, q, nctas)
+                          : cot_kp<T, EXACT, K, false>(L, t, b0, b1, q, nctas);
+}
+
+template <class T, bool EXACT, int K, bool PER>
+int occ_kp(const TileGeo& t) {
     const size_t sm = smem_t<T>(t);
-    cudaError_t e = cudaFuncSetAttribute(cot_kernel<T, EXACT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    cot_kernel<T, EXACT, K><<<nctas, 32 * t.nwarps, sm, L.stream>>>((T*)b0, (T*)b1, L.geo, coeffs_as<T>(L.coeffs), t,
-                                                                    vec_aligned<T>(L.geo, b0, b1), q);
-    return cudaGetLastError();
+    if (cudaFuncSetAttribute(cot_kernel<T, EXACT, K, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+        return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cot_kernel<T, EXACT, K, PER>, 32 * t.nwarps, sm) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
 }
 
 template <class T, bool EXACT, int K>
-int occ_k(const TileGeo& t) {
-    const size_t sm = smem_t<T>(t);
-    if (cudaFuncSetAttribute(cot_kernel<T, EXACT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-        return 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cot_kernel<T, EXACT, K>, 32 * t.nwarps, sm) != cudaSuccess)
-        return 1;
-    return n > 0 ? n : 1;
+int occ_k(const LaunchCtx& L, const TileGeo& t) {
+    return L.geo.periodic ? occ_kp<T, EXACT, K, true>(t) : occ_kp<T, EXACT, K, false>(t);
 }
 
 }  // namespace
@@ -429,7 +458,7 @@ cudaError_t cot(const LaunchCtx& L, const TileGeo& t, void* b0, void* b1, const 
 }
 
 int ctas_per_sm(const LaunchCtx& L, const TileGeo& t) {
-    PCOT_DISPATCH3(occ_k, t)
+    PCOT_DISPATCH3(occ_k, L, t)
     return 1;
 }
 
