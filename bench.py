@@ -37,7 +37,6 @@ UNIT = "GUpdates/s"
 # Tile parameters of the timed schedule (from the autotuner's sweep on GB300).
 BEST = {"schedule": "cot", "tile": (80, 112), "time_depth": 8, "cot_threshold": (2, 256, 256)}
 BEST_SLT = {"schedule": "slt", "tile": (40, 112), "time_depth": 4, "cot_threshold": (2, 256, 256)}
-BATCH = {"tile": (96, 112), "time_depth": 6, "cot_threshold": (2, 256, 256)}
 # Depths (with their best tile heights) scanned beside the headline.
 DEPTH_SCAN = [(2, (80, 112)), (4, (80, 112)), (6, (96, 112)), (8, (80, 112))]
 WORKLOAD = "heat2d-5pt 8192x8192 T=512 fp32 zero-Dirichlet"
@@ -647,11 +646,13 @@ def run_la(pcot, h, stream, steps):
 def run_batched(pcot, stream, steps):
     """256 independent Heat-2D grids (sides log-uniform in [256, 2048], T in
     [64, 1024], seeded) advanced by one persistent launch replayed from a CUDA
-    graph: throughput and per-grid completion latency (p50 / p99)."""
+    graph: throughput and per-grid completion latency (p50 / p99).  The tile
+    shape is the autotuner's pick, timed on this batch (`tuner.tune_batched`)."""
     import numpy as np
     import torch
 
     import seeded_inputs as si
+    from paper_1802_00166_gb300 import tuner
     probs = si.batched_problem_set(seed=4, count=256)
     h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
     grids, sizes, strides, Ts = [], [], [], []
@@ -667,8 +668,8 @@ def run_batched(pcot, stream, steps):
         strides += [pitch, 1]
         Ts.append(T)
         updates += float(side) * side * T
-    params = [pcot.tile_params(tile=BATCH["tile"], time_depth=BATCH["time_depth"],
-                               cot_threshold=BATCH["cot_threshold"])] * len(probs)
+    best, tried = tuner.tune_batched(h, grids, sizes, strides, Ts, pcot.PCOT_F32, stream)
+    params = [pcot.tile_params(**best)] * len(probs)
     nb = pcot.pcot_batch_workspace_bytes(h, sizes, strides, Ts, pcot.PCOT_F32, params)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     done = torch.zeros(len(probs) + 1, dtype=torch.int64, device="cuda")
@@ -693,7 +694,9 @@ def run_batched(pcot, stream, steps):
     lat = (d[1:] - d[0]) / 1e6
     return {"grids": len(probs), "updates": updates, "ms": ms, "GUpdates/s": updates / ms / 1e6,
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
-            "latency_ms_max": float(lat.max()), "params": BATCH, "launch": "one persistent kernel, CUDA graph"}
+            "latency_ms_max": float(lat.max()), "launch": "one persistent kernel, CUDA graph",
+            "params": {a: list(v) if isinstance(v, tuple) else v for a, v in best.items()},
+            "tuned": [{"tile": list(c["tile"]), "time_depth": c["time_depth"], "ms": round(ms, 3)} for c, ms in tried]}
 
 
 def compare_schedules(pcot, h, base, sizes, strides, stream):

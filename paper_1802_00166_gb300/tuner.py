@@ -152,6 +152,49 @@ def tune_problem(prob, dtype=pcot.PCOT_F32, reps=2, cands=None, stream=None):
         pcot.pcot_destroy(h)
 
 
+def batch_candidates():
+    """Tile shapes explored for a batched launch (one shape for every grid of
+    the launch): the persistent-order depths and tile heights of the 2-D set."""
+    return [dict(tile=(H, 112), time_depth=k, cot_threshold=(2, 256, 256)) for k in (4, 6, 8)
+            for H in (64, 80, 96, 128)]
+
+
+def tune_batched(h, grids, sizes, strides, Ts, dtype, stream, cands=None, reps=2):
+    """The exhaustive autotuner applied to a batch: every candidate shape is
+    timed on the batch itself (one warm-up launch, then `reps` launches between
+    CUDA events).  Returns (best candidate, [(candidate, ms per launch)])."""
+    import torch
+    cands = cands or batch_candidates()
+    results = []
+    for c in cands:
+        params = [pcot.tile_params(**c)] * len(Ts)
+        try:
+            nb = pcot.pcot_batch_workspace_bytes(h, sizes, strides, Ts, dtype, params)
+        except pcot.PcotError:
+            continue
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        done = torch.zeros(len(Ts) + 1, dtype=torch.int64, device="cuda")
+        b = pcot.pcot_batch_create(h, grids, sizes, strides, Ts, dtype, params, ws, nb, done, stream)
+        try:
+            pcot.pcot_batch_launch(b, stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                pcot.pcot_batch_launch(b, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = pcot.pcot_check(h, stream)
+        finally:
+            pcot.pcot_batch_destroy(b)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "tune_batched")
+        results.append((c, e0.elapsed_time(e1) / reps))
+    if not results:
+        raise ValueError("tune_batched: no candidate fits this batch")
+    return min(results, key=lambda r: r[1])[0], results
+
+
 def records_for(prob, cands, ms, feats, dtype=pcot.PCOT_F32):
     rows_x, rows_y = [], []
     for (sched, p), t, f in zip(cands, ms, feats):
