@@ -27,12 +27,14 @@ def _tile_nonempty(kind, n, b, kb, ib, jb):
     return False
 
 
-def _rule_edges(kind, n, b):
+def _rule_edges(kind, n, b, ne=None):
     """Edges of the blocked algorithm's tile graph: a block's next update
     waits for its previous one, a panel for its diagonal block, an update for
-    the panels it reads (Cholesky reads column block ib and column block jb)."""
+    the panels it reads (Cholesky reads column block ib and column block jb).
+    `ne`: the non-empty tiles (found point by point when not given)."""
     L = -(-n // b)
-    ne = {t for t in itertools.product(range(L), repeat=3) if _tile_nonempty(kind, n, b, *t)}
+    if ne is None:
+        ne = {t for t in itertools.product(range(L), repeat=3) if _tile_nonempty(kind, n, b, *t)}
     edges = set()
     for kb, ib, jb in ne:
         preds = [(kb - 1, ib, jb)]
@@ -142,35 +144,20 @@ def test_planner_dependency_counts(kind, n, b):
     (whose coverage of the point dependences is checked above)."""
     q = pcot.pcot_la_plan_query(KINDS[kind], n, pcot.PCOT_COT, pcot.tile_params(tile=(b, 0, 0)))
     L = q["L"]
-    ne, edges = _rule_edges(kind, n, b) if n <= 97 else (None, None)
-    if edges is None:
-        # larger n: nonemptiness in closed form (all tiles of the pyramid hold points
-        # except an LU diagonal tile of a one-row last block)
+    if n <= 97:
+        ne, edges = _rule_edges(kind, n, b)
+    else:
+        # larger n: non-emptiness in closed form (every tile of the pyramid holds
+        # points except an LU diagonal tile of a one-row last block)
         ne = set()
-        for t in itertools.product(range(L), repeat=3):
-            kb, ib, jb = t
+        for kb, ib, jb in itertools.product(range(L), repeat=3):
             if kind == "lu":
                 ok = ib >= kb and jb >= kb and not (ib == kb and min(n, (kb + 1) * b) - kb * b < 2)
             else:
                 ok = kb <= jb <= ib
             if ok:
-                ne.add(t)
-        _, edges = set(), set()
-        for kb, ib, jb in ne:
-            preds = [(kb - 1, ib, jb)]
-            if kind == "lu":
-                if (ib, jb) != (kb, kb) and (ib == kb or jb == kb):
-                    preds.append((kb, kb, kb))
-                if ib > kb and jb > kb:
-                    preds += [(kb, ib, kb), (kb, kb, jb)]
-            else:
-                if jb == kb and ib > kb:
-                    preds.append((kb, kb, kb))
-                if jb > kb:
-                    preds += [(kb, ib, kb), (kb, jb, kb)]
-            for pr in preds:
-                if pr in ne:
-                    edges.add((pr, (kb, ib, jb)))
+                ne.add((kb, ib, jb))
+        ne, edges = _rule_edges(kind, n, b, ne)
     indeg = np.zeros(L ** 3, dtype=np.int64)
     for _, c in edges:
         indeg[(c[0] * L + c[1]) * L + c[2]] += 1
