@@ -14,6 +14,9 @@ Contents
                      Pinned by bitwise equality with ``sweep``.
   * ``orthant_empty`` / ``padded_box``  the pieces of that recursion.
   * ``grid_sum``     correctly rounded sum of the interior (math.fsum).
+  * ``max_rel_error`` / ``pointwise_rel_error`` / ``errors``  the FP32 error
+                     measures against the FP64 result: normwise, and per cell
+                     with a floor of 1e-3 of the grid's maximum.
   * ``mlp``          FP64 MLP forward/backward/Adam (module ``oracle.mlp``).
   * ``legality``     tile-level hazard checker for tile queues (``oracle.legality``).
   * ``gs2d`` / ``gs2d_pcot`` / ``gs2d_box_empty`` / ``gs2d_tile_order``
@@ -359,3 +362,32 @@ def max_rel_error(u, ref):
     den = float(np.max(np.abs(ref))) if ref.size else 0.0
     num = float(np.max(np.abs(u - ref))) if ref.size else 0.0
     return num / den if den > 0 else num
+
+
+POINTWISE_FLOOR = 1e-3
+
+
+def pointwise_rel_error(u, ref, floor=POINTWISE_FLOOR):
+    """Pointwise error max_x |u(x) - ref(x)| / max(|ref(x)|, floor * max|ref|).
+
+    The normwise error divides every difference by the largest value of the
+    grid, so a wrong value in a cell far below that maximum can hide under
+    it; this measure divides each cell's difference by the cell's own
+    magnitude, floored at `floor` times the maximum so that cells at or near
+    zero do not divide by zero."""
+    u = np.asarray(u, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.size == 0:
+        return 0.0
+    a = np.abs(ref)
+    top = float(np.max(a))
+    if top == 0.0:
+        return float(np.max(np.abs(u - ref)))
+    den = np.maximum(a, floor * top)
+    return float(np.max(np.abs(u - ref) / den))
+
+
+def errors(u, ref, floor=POINTWISE_FLOOR):
+    """Both error measures of a result against the FP64 reference."""
+    return {"normwise": max_rel_error(u, ref), "pointwise": pointwise_rel_error(u, ref, floor),
+            "pointwise_floor": floor}

@@ -37,3 +37,14 @@ def hand_steps():
             init=np.array([float(v) for v in b["init"].split()]).reshape(shape),
             expected=np.array([float(v) for v in b["expected"].split()]).reshape(shape)))
     return out
+
+
+def pcot_orders():
+    out = []
+    for b in load_blocks("pcot_order.txt"):
+        sizes = tuple(int(v) for v in b["sizes"].split())
+        vals = np.array([int(v) for v in b["order"].split()], dtype=np.int64)
+        out.append(dict(name=b["name"], sizes=sizes, T=int(b["T"]),
+                        leaf=tuple(int(v) for v in b["leaf"].split()),
+                        order=vals.reshape(-1, len(sizes) + 1)))
+    return out

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import golden
 import seeded_inputs as si
 
 HEAT2D = [0.5, 0.125, 0.125, 0.125, 0.125]
@@ -118,3 +119,47 @@ def test_early_exits_taken(oracle_lib):
     assert st["zero_exits"] > 0
     assert st["empty_exits"] > 0
     assert st["points"] == 20 * 20 * 12
+
+
+def _run_points(init, sizes, coeffs, T, order):
+    """Execute the points (t, i...) in the given order with the two-buffer
+    t%2 storage; returns the grid after T steps (Dirichlet ring kept)."""
+    X = [init.copy(), init.copy()]
+    d = len(sizes)
+    for rec in order:
+        t, i = int(rec[0]), [int(v) + 1 for v in rec[1:]]
+        src, dst = X[(t - 1) % 2], X[t % 2]
+        v = coeffs[0] * src[tuple(i)]
+        for a in range(d):
+            for k, o in enumerate((-1, 1)):
+                j = list(i)
+                j[a] += o
+                v = v + coeffs[1 + 2 * a + k] * src[tuple(j)]
+        dst[tuple(i)] = v
+    return X[T % 2]
+
+
+@pytest.mark.parametrize("case", golden.pcot_orders(), ids=lambda c: c["name"])
+def test_pcot_order_hand_derived(oracle_lib, case):
+    """The recursion's visit order equals the hand-derived one (Sec. 4.2:
+    lexicographic children, time bit most significant, zero and empty
+    orthants skipped, lexicographic leaves)."""
+    got = oracle.pcot_order(case["sizes"], case["T"], case["leaf"])
+    assert np.array_equal(got, case["order"])
+
+
+def test_pcot_order_pin_catches_a_legal_sibling_swap(oracle_lib):
+    """Plant a wrong order on the CPU: run the two independent spatial
+    siblings B and C of the 2-D case in swapped order.  The values do not
+    change (the swap is legal), so only the order pin can catch it."""
+    case = [c for c in golden.pcot_orders() if c["name"] == "order_2d_n3x3_T2"][0]
+    order = case["order"]
+    b_lo, c_lo, d_lo = 5, 9, 13           # leaves B = rows 5..8, C = rows 9..12
+    swapped = np.concatenate([order[:b_lo], order[c_lo:d_lo], order[b_lo:c_lo], order[d_lo:]])
+    sizes, T = case["sizes"], case["T"]
+    g = si.uniform_grid(sizes, 5, ring="random")
+    ref = oracle.sweep(g, sizes, HEAT2D, T)
+    assert np.array_equal(_run_points(g, sizes, HEAT2D, T, order), ref)
+    assert np.array_equal(_run_points(g, sizes, HEAT2D, T, swapped), ref)   # legal: same values
+    assert not np.array_equal(swapped, case["order"])                       # ... but the pin fails
+    assert np.array_equal(oracle.pcot_order(sizes, T, case["leaf"]), case["order"])

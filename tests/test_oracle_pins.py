@@ -166,3 +166,25 @@ def test_max_rel_error_definition():
     ref = np.array([1.0, -4.0, 2.0])
     u = np.array([1.0, -4.0 + 2e-5, 2.0])
     assert oracle.max_rel_error(u, ref) == pytest.approx(2e-5 / 4.0)
+
+
+def test_pointwise_rel_error_definition():
+    """Hand-computed cases of the floored pointwise error: a cell's own
+    magnitude divides its difference; cells below 1e-3 of the maximum use
+    that floor instead."""
+    ref = np.array([4.0, 0.5, 1e-6, -2.0])
+    u = ref + np.array([0.0, 1e-6, 2e-9, -4e-6])
+    # per cell: 0/4, 1e-6/0.5, 2e-9/max(1e-6, 4e-3), 4e-6/2
+    assert oracle.pointwise_rel_error(u, ref) == pytest.approx(2e-6)
+    # a wrong small cell that the normwise measure does not see
+    bad = ref.copy()
+    bad[1] += 2e-5
+    assert oracle.max_rel_error(bad, ref) == pytest.approx(5e-6)
+    assert oracle.pointwise_rel_error(bad, ref) == pytest.approx(4e-5)
+    # below the floor: the floor divides
+    tiny = ref.copy()
+    tiny[2] += 4e-8
+    assert oracle.pointwise_rel_error(tiny, ref) == pytest.approx(1e-5)
+    e = oracle.errors(u, ref)
+    assert e["normwise"] == pytest.approx(1e-6) and e["pointwise"] == pytest.approx(2e-6)
+    assert oracle.pointwise_rel_error(np.zeros(3), np.zeros(3)) == 0.0
