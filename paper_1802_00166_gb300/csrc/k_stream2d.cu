@@ -44,11 +44,19 @@ struct Shape {
 };
 
 // FP32 warps fed by TMA evaluate the update two cells at a time with the packed
-// f32x2 multiply and fused multiply-add (same per-cell rounding and operand
-// order as the scalar path, so the results are bitwise unchanged).  A lane's
-// four columns c0..c3 are stored as the pairs (c0, c2) and (c1, c3): then the
-// west neighbours of (c1, c3) and the east neighbours of (c0, c2) are existing
-// pairs, and only (w, c1) and (c2, e) have to be assembled per stage.
+// f32x2 multiply and fused multiply-add.  A lane's four columns c0..c3 are
+// held in their natural order as the pairs P = (c0, c1) and Q = (c2, c3),
+// exactly as a 16-byte vector load delivers them and a 16-byte store takes
+// them.  The centre, north and south terms are whole pairs (packed); the west
+// and east neighbours of a pair are shifted by one column -- (c-1, c0),
+// (c1, c2), (c3, c4) -- and are applied as scalar FMAs on the halves of the
+// running pair sums.  Assembling the shifted operands into register pairs
+// instead took 3.5 register moves per stage and lane, and reordering the
+// columns into (c0, c2), (c1, c3) pairs around every load and store another
+// 14 per row; the compiler issued most of those moves as integer
+// multiply-adds on the FMA pipe that the stencil itself saturates.  Every
+// cell still sees the same rounded operations in the same order as the
+// scalar path, so the results are bitwise unchanged.
 //
 // Boundary warps (CHECK: Dirichlet pass-through, partial stores) of the
 // launch-per-block kernels run the same unrolled TMA loop as interior warps:
@@ -62,12 +70,6 @@ constexpr bool kUnrolledCheck = !CG;
 
 template <class T, bool EXACT, bool CHECK, bool TMA, bool CG>
 constexpr bool kPacked = std::is_same<T, float>::value && !EXACT && TMA && (!CHECK || kUnrolledCheck<CG>);
-
-// Register slot of lane column j (identity unless packed).
-template <bool PK>
-__device__ __forceinline__ constexpr int slot_of(int j) {
-    return PK ? (j == 1 ? 2 : j == 2 ? 1 : j) : j;
-}
 
 template <class T>
 struct Args {
@@ -197,9 +199,10 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
 
     constexpr bool PK = kPacked<T, EXACT, CHECK, TMA, CG>;
     static_assert(!PK || E == 4, "packed path assumes four columns per lane");
-    float2 k2[5];
+    float2 k2[3];  // centre, north, south as pairs; west and east as scalars
 #pragma unroll
-    for (int c = 0; c < 5; ++c) k2[c] = make_float2((float)A.c.c[c], (float)A.c.c[c]);
+    for (int c = 0; c < 3; ++c) k2[c] = make_float2((float)A.c.c[c], (float)A.c.c[c]);
+    const float kw = (float)A.c.c[3], ke = (float)A.c.c[4];
 
     T R[K][3][E];
 #pragma unroll
@@ -245,27 +248,30 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             if constexpr (PK) {
-                // slots: 0 = c0, 1 = c2, 2 = c1, 3 = c3
+                // P = (c0, c1), Q = (c2, c3); operand order of upd2 in the
+                // FMA modes: centre, north, west, east, and the south row
+                // (this step's output of the previous stage) last
                 const float wl = __shfl_up_sync(kFull, R[s][SB][3], 1);    // c3 of the lane to the west
                 const float er = __shfl_down_sync(kFull, R[s][SB][0], 1);  // c0 of the lane to the east
-                const float2 cA = make_float2(R[s][SB][0], R[s][SB][1]);   // (c0, c2)
-                const float2 cB = make_float2(R[s][SB][2], R[s][SB][3]);   // (c1, c3)
-                // operand order of upd2 in the FMA modes: the south row (this
-                // step's output of the previous stage) enters last
-                float2 oA = __fmul2_rn(k2[0], cA);
-                oA = __ffma2_rn(k2[1], make_float2(R[s][SA][0], R[s][SA][1]), oA);
-                oA = __ffma2_rn(k2[3], make_float2(wl, R[s][SB][2]), oA);   // west of (c0, c2)
-                oA = __ffma2_rn(k2[4], cB, oA);                              // east of (c0, c2)
-                oA = __ffma2_rn(k2[2], make_float2(R[s][SN][0], R[s][SN][1]), oA);
-                float2 oB = __fmul2_rn(k2[0], cB);
-                oB = __ffma2_rn(k2[1], make_float2(R[s][SA][2], R[s][SA][3]), oB);
-                oB = __ffma2_rn(k2[3], cA, oB);                              // west of (c1, c3)
-                oB = __ffma2_rn(k2[4], make_float2(R[s][SB][1], er), oB);   // east of (c1, c3)
-                oB = __ffma2_rn(k2[2], make_float2(R[s][SN][2], R[s][SN][3]), oB);
-                out[0] = oA.x;
-                out[1] = oA.y;
-                out[2] = oB.x;
-                out[3] = oB.y;
+                const float* b = R[s][SB];
+                float2 oP = __fmul2_rn(k2[0], make_float2(b[0], b[1]));
+                oP = __ffma2_rn(k2[1], make_float2(R[s][SA][0], R[s][SA][1]), oP);
+                oP.x = __fmaf_rn(kw, wl, oP.x);
+                oP.y = __fmaf_rn(kw, b[0], oP.y);
+                oP.x = __fmaf_rn(ke, b[1], oP.x);
+                oP.y = __fmaf_rn(ke, b[2], oP.y);
+                oP = __ffma2_rn(k2[2], make_float2(R[s][SN][0], R[s][SN][1]), oP);
+                float2 oQ = __fmul2_rn(k2[0], make_float2(b[2], b[3]));
+                oQ = __ffma2_rn(k2[1], make_float2(R[s][SA][2], R[s][SA][3]), oQ);
+                oQ.x = __fmaf_rn(kw, b[1], oQ.x);
+                oQ.y = __fmaf_rn(kw, b[2], oQ.y);
+                oQ.x = __fmaf_rn(ke, b[3], oQ.x);
+                oQ.y = __fmaf_rn(ke, er, oQ.y);
+                oQ = __ffma2_rn(k2[2], make_float2(R[s][SN][2], R[s][SN][3]), oQ);
+                out[0] = oP.x;
+                out[1] = oP.y;
+                out[2] = oQ.x;
+                out[3] = oQ.y;
             } else {
                 const T wl = __shfl_up_sync(kFull, R[s][SB][E - 1], 1);
                 const T er = __shfl_down_sync(kFull, R[s][SB][0], 1);
@@ -277,14 +283,13 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 }
             }
             if constexpr (CHECK) {
-                // Dirichlet pass-through; slot j holds column slot_of(j)
-                // (the slot map is its own inverse)
+                // Dirichlet pass-through
                 const int rr = i - s - 1;
                 const bool rint = rr >= rlo && rr <= rhi;
                 if (!(rint && warp_xint)) {
 #pragma unroll
                     for (int j = 0; j < E; ++j)
-                        if (!(rint && xint[slot_of<PK>(j)])) out[j] = R[s][SB][j];
+                        if (!(rint && xint[j])) out[j] = R[s][SB][j];
                 }
             }
             if (s + 1 < K) {
@@ -302,12 +307,12 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
                 V q;
                 T* qq = reinterpret_cast<T*>(&q);
 #pragma unroll
-                for (int j = 0; j < E; ++j) qq[j] = out[slot_of<PK>(j)];
+                for (int j = 0; j < E; ++j) qq[j] = out[j];
                 *reinterpret_cast<V*>(rowp) = q;
             } else if (any_st) {
 #pragma unroll
                 for (int j = 0; j < E; ++j)
-                    if (st[j]) rowp[j] = out[slot_of<PK>(j)];
+                    if (st[j]) rowp[j] = out[j];
             }
         }
     };
@@ -328,10 +333,10 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             const V q = *reinterpret_cast<const V*>(ring + (lane_ring + slot * A.slot_elems + r * A.BW));
             const T* qq = reinterpret_cast<const T*>(&q);
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
+            for (int j = 0; j < E; ++j) R[0][SN][j] = qq[j];
         } else {
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = pf[U][j];
+            for (int j = 0; j < E; ++j) R[0][SN][j] = pf[U][j];
             if (i + 3 < nrows) load_row(ybeg + i + 3, pf[U]);
         }
         const Row out = stages(Uc, i);
@@ -381,7 +386,7 @@ __device__ __forceinline__ void warp_tile(const Args<T>& A, const CUtensorMap* t
             const V q = *reinterpret_cast<const V*>(src_row);
             const T* qq = reinterpret_cast<const T*>(&q);
 #pragma unroll
-            for (int j = 0; j < E; ++j) R[0][SN][slot_of<PK>(j)] = qq[j];
+            for (int j = 0; j < E; ++j) R[0][SN][j] = qq[j];
             store(ii, out_row, stages(Uc, ii));
         };
         T* orow = dst_row0;
