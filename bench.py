@@ -432,17 +432,40 @@ def run_gpu(args):
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
-    if rank == 0 and not args.no_cpu_baseline:
-        v, steps, cores = _cpu_oracle_sample()
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}
-    if args.schedules and rank == 0:
-        line["schedules"] = compare_schedules(pcot, h, base, sizes, strides, stream)
-    if (args.batched or args.gs2d or args.fdtd2d or args.la) and rank == 0:
-        del base, wsbuf, host
+
+    # Everything below runs after the timed region and leaves `value` alone.
+    extra = rank == 0 and not args.schedule
+    final = None
+    if extra:
+        # The headline configuration once more from the seeded initial grid,
+        # for the error against the FP64 oracle (computed in the CPU leg).
+        view.copy_(torch.from_numpy(g0).cuda())
+        step()
+        torch.cuda.synchronize()
+        final = view.cpu().numpy()
+        line["vs_sweep"] = compare_schedules(pcot, h, base, sizes, strides, stream)
+    configs = {}
+    if extra:
+        del wsbuf, host
+        base = view = None
         torch.cuda.empty_cache()
-    if args.batched and rank == 0:
-        line["batched"] = run_batched(pcot, stream, args.steps)
+        j1, j1_out = run_jacobi1d(pcot, stream, args.steps)
+        j3, j3_out = run_jacobi3d(pcot, stream, args.steps, peak)
+        configs = {"jacobi1d": j1, "jacobi3d": j3, "batched": run_batched(pcot, stream, args.steps)}
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, ref = _cpu_oracle_heat2d(g0, full=extra)
+        line["cpu_baseline"] = cpu
+        if final is not None and ref is not None:
+            import oracle
+            err = oracle.errors(oracle.interior(final, sizes), oracle.interior(ref, sizes))
+            line["error"] = dict(err, vs="FP64 oracle run on the widened FP32 inputs", T=T_STEPS,
+                                 bound=1e-5)
+        if extra:
+            _cpu_leg_configs(configs, j1_out, j3_out)
+    if configs:
+        line["configs"] = configs
+    if (args.gs2d or args.fdtd2d or args.la) and rank == 0:
+        torch.cuda.empty_cache()
     if args.gs2d and rank == 0:
         line["gs2d"] = run_gs2d(pcot, h, stream, args.steps)
     if args.fdtd2d and rank == 0:
@@ -455,6 +478,164 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# Jacobi-1D 3-point, FP64 exact, n = 4096, T = 1024, weights 1/3, seeded ring.
+J1D_RUNS = [("sweep", None), ("slt", dict(tile=(32,), time_depth=16)),
+            ("cot", dict(tile=(64,), time_depth=16, cot_threshold=(4, 4)))]
+# Jacobi-3D 7-point, 512^3 periodic FP32, T = 128, Fourier-mode input.
+J3D_RUNS = [("sweep", None, 1), ("slt_k2", dict(tile=(64, 56, 0), time_depth=2), 2),
+            ("slt_k3", dict(tile=(64, 56, 0), time_depth=3), 3),
+            ("slt_k4", dict(tile=(64, 56, 0), time_depth=4), 4)]
+J3D_HEAD = "slt_k4"
+
+
+def _time_runs(run, reps, stream):
+    import torch
+    run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_jacobi1d(pcot, stream, steps):
+    """Jacobi-1D at the configuration's size on every schedule, FP64 exact
+    mode; results kept for the bitwise check against the oracle."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    n, T = 4096, 1024
+    h = pcot.pcot_create(1, 1, [1.0 / 3.0] * 3, pcot.PCOT_DIRICHLET)
+    g = si.uniform_grid((n,), 1, ring="random")
+    dev = torch.from_numpy(g.copy()).cuda()
+    out, results = {"workload": "jacobi1d-3pt n=4096 T=1024 fp64-exact Dirichlet (seeded ring)"}, {}
+    for name, prm in J1D_RUNS:
+        sched = pcot.SCHEDULES[name]
+        p = pcot.tile_params(**prm) if prm else None
+        nb = pcot.pcot_workspace_bytes(h, (n,), None, T, pcot.PCOT_F64_EXACT, sched, p)
+        ws = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
+        run = lambda: pcot.pcot_run(h, dev.data_ptr(), ws.data_ptr(), nb, (n,), None, T, pcot.PCOT_F64_EXACT,
+                                    sched, p, stream)
+        ms = _time_runs(run, max(5, min(steps, 20)), stream)
+        dev.copy_(torch.from_numpy(g))
+        run()
+        st = pcot.pcot_check(h, stream)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "jacobi1d " + name)
+        results[name] = dev.cpu().numpy()
+        out[name] = {"ms": ms, "GUpdates/s": n * T / ms / 1e6, "params": prm}
+        dev.copy_(torch.from_numpy(g))
+    pcot.pcot_destroy(h)
+    return out, (g, results)
+
+
+def run_jacobi3d(pcot, stream, steps, peak):
+    """Jacobi-3D 512^3 periodic FP32 (T = 128, 8 seeded Fourier modes): the
+    sweep and the single-level schedule at depths 2-4, each with the fraction
+    of its temporal-blocking HBM roof; the depth-4 result is kept for the
+    error against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import seeded_inputs as si
+    n, T = 512, 128
+    sizes = (n, n, n)
+    h = pcot.pcot_create(3, 1, [0.4] + [0.1] * 6, pcot.PCOT_PERIODIC)
+    g64, _ = si.fourier_grid(sizes, 3)
+    g32 = g64.astype(np.float32)
+    del g64
+    dev = torch.from_numpy(g32).cuda()
+    grid_bytes = 2.0 * n ** 3 * 4
+    out = {"workload": "jacobi3d-7pt 512^3 T=128 fp32 periodic (8 Fourier modes)", "head": J3D_HEAD}
+    result = None
+    for name, prm, k in J3D_RUNS:
+        sched = pcot.PCOT_SWEEP if prm is None else pcot.PCOT_SLT
+        p = pcot.tile_params(**prm) if prm else None
+        nb = pcot.pcot_workspace_bytes(h, sizes, None, T, pcot.PCOT_F32, sched, p)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        run = lambda: pcot.pcot_run(h, dev.data_ptr(), ws.data_ptr(), nb, sizes, None, T, pcot.PCOT_F32, sched, p,
+                                    stream)
+        ms = _time_runs(run, max(3, min(steps, 10)), stream)
+        t_roof = math.ceil(T / k) * grid_bytes / (peak * 1e9) * 1e3
+        out[name] = {"ms": ms, "GUpdates/s": n ** 3 * T / ms / 1e6, "time_depth": k,
+                     "roofline_frac": t_roof / ms, "params": prm}
+        if name == J3D_HEAD:
+            dev.copy_(torch.from_numpy(g32))
+            run()
+            torch.cuda.synchronize()
+            result = dev.cpu().numpy()
+            dev.copy_(torch.from_numpy(g32))
+        st = pcot.pcot_check(h, stream)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "jacobi3d " + name)
+        del ws
+    pcot.pcot_destroy(h)
+    del dev
+    torch.cuda.empty_cache()
+    return out, (g32, result)
+
+
+def _cpu_oracle_heat2d(g0, full=True, seconds=12.0):
+    """CPU leg: the oracle (naive FP64 sweep, OpenMP over rows, all host
+    cores) on the benchmark grid.  With `full`, all 512 steps when they fit
+    about a minute, and the result is returned for the error of the GPU run;
+    otherwise a bounded number of steps.  Returns (cpu_baseline, result)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sizes = (N_SIDE, N_SIDE)
+    g = g0.astype("float64")
+    oracle.sweep(g, sizes, HEAT2D, 1, threads=cores)      # warm-up: threads, first-touch pages
+    t0 = time.perf_counter()
+    oracle.sweep(g, sizes, HEAT2D, 2, threads=cores)
+    one = (time.perf_counter() - t0) / 2
+    if full and one * T_STEPS <= 90.0:
+        t0 = time.perf_counter()
+        ref = oracle.sweep(g, sizes, HEAT2D, T_STEPS, threads=cores)
+        dt = time.perf_counter() - t0
+        return ({"value": N_SIDE * N_SIDE * T_STEPS / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                 "sample": f"full 8192^2 grid, all {T_STEPS} steps of the FP64 naive sweep"}, ref)
+    steps = max(1, min(64, int(seconds / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.sweep(g, sizes, HEAT2D, steps, threads=cores)
+    dt = time.perf_counter() - t0
+    return ({"value": N_SIDE * N_SIDE * steps / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"full 8192^2 grid, {steps} steps of the FP64 naive sweep"}, None)
+
+
+def _cpu_leg_configs(configs, j1_out, j3_out):
+    """CPU leg for the other configurations: the oracle timed on each, its
+    results compared with the GPU's (Jacobi-1D bitwise, Jacobi-3D error)."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    g, results = j1_out
+    t0 = time.perf_counter()
+    ref = oracle.sweep(g, (4096,), [1.0 / 3.0] * 3, 1024, threads=1)
+    dt = time.perf_counter() - t0
+    c1 = configs["jacobi1d"]
+    c1["cpu_baseline"] = {"value": 4096 * 1024 / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": "the whole configuration on one core"}
+    c1["bitwise_equal_to_oracle"] = {k: bool(np.array_equal(v, ref)) for k, v in results.items()}
+    g32, res = j3_out
+    n, T = 512, 128
+    t0 = time.perf_counter()
+    ref = oracle.sweep(g32, (n, n, n), [0.4] + [0.1] * 6, T, periodic=True, threads=cores)
+    dt = time.perf_counter() - t0
+    c3 = configs["jacobi3d"]
+    c3["cpu_baseline"] = {"value": n ** 3 * T / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                          "sample": "the whole configuration (FP64 naive sweep)"}
+    if res is not None:
+        c3["error"] = dict(oracle.errors(res, ref), vs="FP64 oracle run on the widened FP32 inputs",
+                           schedule=J3D_HEAD, bound=1e-5)
 
 
 GS2D = {"n": 2000, "T": 500, "slt": {"tile": (32, 128), "time_depth": 8},
@@ -744,6 +925,23 @@ def compare_schedules(pcot, h, base, sizes, strides, stream):
         if p is not None:
             out[name]["params"] = {"tile": list(p.tile)[:2], "time_depth": p.time_depth,
                                    "cot_threshold": list(p.cot_threshold)[:3]}
+        # DRAM bytes per update from the committed ncu capture of this kernel
+        # (null once the kernel sources changed since it was taken).
+        q = pcot.pcot_plan_query(h, sizes, T_STEPS, pcot.PCOT_F32, p, with_queue=False) if p else None
+        if sched == pcot.PCOT_SWEEP:
+            tag, per_update_blocks = "sweep2d_vec_kernel f32 k=1 tile=[0, 0]", T_STEPS
+        else:
+            kk = q["depth"]
+            kern = "slt_kernel" if sched == pcot.PCOT_SLT else "cot_kernel"
+            tag, per_update_blocks = f"{kern} f32 k={kk} tile={q['tile_ext'][:2]}", T_STEPS // kk
+        traffic = _traffic_from_profile(tag, per_update_blocks)
+        out[name]["dram_bytes_per_update"] = traffic / (N_SIDE * N_SIDE * T_STEPS) if traffic else None
+    sw = out["sweep_f32"]
+    for name in out:
+        if name != "sweep_f32":
+            out[name]["speedup_vs_sweep"] = sw["ms"] / out[name]["ms"]
+            a, b = out[name].get("dram_bytes_per_update"), sw.get("dram_bytes_per_update")
+            out[name]["dram_bytes_vs_sweep"] = a / b if a and b else None
     return out
 
 
@@ -818,9 +1016,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--schedule", default=None, choices=[None, "sweep", "slt", "cot"])
-    ap.add_argument("--schedules", action="store_true", help="also time sweep / SLT / COT side by side")
+    ap.add_argument("--schedules", action="store_true", help="(default) sweep / SLT / COT side by side")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched", action="store_true", help="also time the 256-grid batched persistent launch")
+    ap.add_argument("--batched", action="store_true", help="(default) the 256-grid batched persistent launch")
     ap.add_argument("--gs2d", action="store_true", help="also time Gauss-Seidel 2-D at the paper's size")
     ap.add_argument("--fdtd2d", action="store_true", help="also time FDTD-2D at the paper's size")
     ap.add_argument("--la", action="store_true", help="also time LU and Cholesky at the paper's sizes")

@@ -124,7 +124,8 @@ pcot_status pcot_destroy(pcot_handle h);
  * Device workspace needed by pcot_run for this problem, step count and
  * schedule, in bytes (a twin of the grid with the same strides, plus the
  * per-run dependency counters and tile queue of PCOT_COT, which grow with the
- * number of time blocks).  `params` may be NULL (defaults).
+ * number of time blocks).  `params` may be NULL (defaults).  For PCOT_AUTO:
+ * the largest need over the picker's candidates (no GPU needed).
  */
 pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t *sizes, const int64_t *strides,
                                  int64_t T, pcot_dtype dtype, pcot_schedule schedule,
@@ -141,7 +142,11 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t *sizes, const int6
  *  workspace_bytes  size of `workspace`; a smaller size than the schedule
  *             needs returns PCOT_ERR_OOM before anything is launched.
  *  T          number of time steps, T >= 0; T = 0 returns PCOT_OK at once.
- *  schedule   PCOT_AUTO picks with the built-in defaults.
+ *  schedule   PCOT_AUTO runs the schedule and tile parameters pcot_pick
+ *             chooses for this problem (the learned picker, or the
+ *             autotuner when no model is loaded; the first call for a
+ *             problem makes the pick and synchronises, later calls reuse
+ *             it); `params` is then ignored.
  *  params     NULL = defaults.
  * Asynchronous on `stream`; call pcot_check to surface device errors.
  */
@@ -315,37 +320,79 @@ pcot_status pcot_features(pcot_handle h, const int64_t *sizes, int64_t T, pcot_d
                           pcot_schedule schedule, const pcot_tile_params *params, float *out12);
 
 /*
- * Pick the candidate with the least predicted time: builds the features of
- * the ncand candidates, normalises them with mean/std (HOST, 12 + 12
- * floats), runs the MLP forward and argmin kernels, returns the index in
- * *best (HOST).  `scratch` is device memory of at least
- * ncand * (12 + 2) * 4 + 256 bytes.  Synchronous.
+ * The candidates the picker chooses among for this handle's stencil and a
+ * dtype (the GPU counterpart of the tile sizes explored in Sec. 5.1.5): the
+ * plain sweep; the single-level schedule over time depths and tile heights;
+ * for Dirichlet grids the recursive order over depths, tile heights and leaf
+ * orthants.  *count receives their number; with cap >= *count the HOST
+ * arrays `schedules` and `params` receive them (cap = 0 only counts;
+ * a smaller nonzero cap returns PCOT_ERR_OOM).  Needs no GPU.
+ */
+pcot_status pcot_candidates(pcot_handle h, pcot_dtype dtype, int cap, pcot_schedule *schedules,
+                            pcot_tile_params *params, int *count);
+
+/*
+ * Load the picker's model into the handle: mlp_params (9282 floats, layout
+ * above), feat_mean and feat_std (12 floats each, the normalisation of the
+ * pcot_features vector), all HOST memory, copied.  Passing three NULLs
+ * unloads the model, after which pcot_pick falls back to the autotuner.  A
+ * new handle starts with the model the library was built with (trained on
+ * this library's own autotuner records), if any.  Clears the picks cached
+ * by earlier pcot_pick / PCOT_AUTO calls.
+ */
+pcot_status pcot_picker_load(pcot_handle h, const float *mlp_params, const float *feat_mean,
+                             const float *feat_std);
+
+/*
+ * Schedule and tile parameters for a problem (sizes, T, dtype).  With a
+ * model loaded: the MLP predicts the time of every candidate of
+ * pcot_candidates (forward and argmin kernels on the legacy default stream)
+ * and the fastest predicted one is returned.  Without a model: the
+ * exhaustive autotuner (pcot_autotune, two timed runs per candidate) runs on
+ * a scratch grid of the problem's size with rows padded to 128 bytes, which
+ * the call allocates and frees; the fastest measured candidate is returned.
+ * Picks are cached in the handle per problem, so later calls (and PCOT_AUTO
+ * runs) for the same problem return at once.  Synchronous.
  */
 pcot_status pcot_pick(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
-                      const float *mlp_params, const float *feat_mean, const float *feat_std,
-                      int ncand, const pcot_schedule *schedules, const pcot_tile_params *params,
-                      void *scratch, int *best, void *stream);
+                      pcot_schedule *schedule, pcot_tile_params *params);
+
+/*
+ * The picker's building block with an explicit model and candidate list:
+ * builds the features of the ncand candidates, normalises them with
+ * mean/std (HOST, 12 + 12 floats), runs the MLP forward and argmin kernels
+ * with the DEVICE parameters `mlp_params`, returns the index in *best
+ * (HOST).  `scratch` is device memory of at least ncand * (12 + 2) * 4 + 256
+ * bytes.  Synchronous.
+ */
+pcot_status pcot_pick_among(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
+                            const float *mlp_params, const float *feat_mean, const float *feat_std,
+                            int ncand, const pcot_schedule *schedules, const pcot_tile_params *params,
+                            void *scratch, int *best, void *stream);
 
 /* ------------------------------------------------------------------------
- * Allocation-free variant of pcot_run (the paper has no counterpart; it
- * serves callers that may not allocate device memory when they advance a
- * grid: code running while a CUDA graph is captured, hosts that reserve all
- * device memory up front, layers handed only a grid and a stream).
+ * Allocation-free variant of pcot_run (the paper has no counterpart).  It
+ * serves callers that may not allocate device memory at the moment they
+ * advance a grid: hosts that reserve all device memory up front and forbid
+ * allocation afterwards (real-time and embedded systems, services with a
+ * fixed memory budget), and library layers that are handed only a grid and a
+ * stream and may not touch the caller's allocator.
  *
- * Runs PCOT_SWEEP or PCOT_SLT exactly like pcot_run, but the grid's twin
- * is a fixed array of PCOT_NOALLOC_MAX_BYTES bytes that the library
- * reserves on every GPU that loads it, for the life of the process; the call
- * allocates nothing (no cudaMalloc, no host heap).  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Grids whose storage span
- * exceeds PCOT_NOALLOC_MAX_BYTES return PCOT_ERR_OOM; PCOT_COT and
- * PCOT_AUTO return PCOT_ERR_UNSUPPORTED.  All calls on one device share the
- * array: calls whose work overlaps on the GPU (other streams, other threads)
- * race on it and must be serialised by the caller.  The array keeps the
- * previous call's contents; the call rewrites everything it reads (the ring
- * is copied in first).  Tiles use plain loads (no TMA ring), so no device
- * status block is needed; launch errors are returned, pcot_check is not
- * required.
+ * Runs PCOT_SWEEP or PCOT_SLT with pcot_run's depth and tile rules, but the
+ * grid's twin is a fixed array of PCOT_NOALLOC_MAX_BYTES bytes that the
+ * library reserves on every GPU that loads it, for the life of the process;
+ * the call allocates nothing (no cudaMalloc, no host heap).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Grids whose storage span
+ * exceeds PCOT_NOALLOC_MAX_BYTES return PCOT_ERR_OOM; PCOT_COT and PCOT_AUTO
+ * return PCOT_ERR_UNSUPPORTED.  All calls on one device share the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller.  The array keeps the previous
+ * call's contents; the call rewrites every cell it reads (the ring is copied
+ * in first), and only the grid's stored cells are written back (the padding
+ * between rows of a strided grid is left untouched).  Tiles use plain loads
+ * (no TMA ring), so no device status block is needed; launch errors are
+ * returned, pcot_check is not required.
  * ------------------------------------------------------------------------ */
 #define PCOT_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
 

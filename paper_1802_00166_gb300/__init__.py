@@ -136,9 +136,15 @@ def _load():
                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_la_plan_query": (S, [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params),
                                    _I32P, _I32P, _I64P, _I32P, _I32P, ctypes.c_int64]),
-        "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
-                          ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                          ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
+        "pcot_pick_among": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(pcot_tile_params), _VP, ctypes.POINTER(ctypes.c_int), _VP]),
+        "pcot_pick": (S, [_VP, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(pcot_tile_params)]),
+        "pcot_picker_load": (S, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)]),
+        "pcot_candidates": (S, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -158,7 +164,8 @@ def exported_symbols():
             "pcot_launch_count", "pcot_batch_workspace_bytes", "pcot_batch_create", "pcot_batch_launch",
             "pcot_batch_destroy", "pcot_run_batched", "pcot_autotune", "pcot_mlp_param_count",
             "pcot_mlp_scratch_bytes", "pcot_mlp_forward", "pcot_mlp_grad", "pcot_mlp_adam", "pcot_mlp_argmin",
-            "pcot_features", "pcot_pick", "pcot_run_noalloc"]
+            "pcot_features", "pcot_pick", "pcot_pick_among", "pcot_picker_load", "pcot_candidates",
+            "pcot_run_noalloc"]
 
 
 def status_string(s):
@@ -239,7 +246,18 @@ def pcot_run(h, grid, workspace, workspace_bytes, sizes, strides, T, dtype, sche
                           int(dtype), int(schedule), _params(params), _stream(stream)), "pcot_run")
 
 
-NOALLOC_MAX_BYTES = 32 * 1024 * 1024
+def _header_define(name):
+    """Integer value of a `#define NAME (expr)` of include/pcot.h (the C ABI
+    header is the single source of the library's compile-time limits)."""
+    import re
+    with open(os.path.join(os.path.dirname(_HERE), "include", "pcot.h")) as f:
+        m = re.search(r"#define\s+" + name + r"\s+\(([^)]*)\)", f.read())
+    if not m:
+        raise ImportError(f"{name} not found in include/pcot.h")
+    return int(eval(re.sub(r"(\d+)u\b", r"\1", m.group(1)), {"__builtins__": {}}))
+
+
+NOALLOC_MAX_BYTES = _header_define("PCOT_NOALLOC_MAX_BYTES")
 
 
 def pcot_run_noalloc(h, grid, sizes, strides, T, dtype, schedule, params=None, stream=None):
@@ -490,15 +508,55 @@ def pcot_features(h, sizes, T, dtype, schedule, params=None):
     return np.array(list(out), dtype=np.float32)
 
 
-def pcot_pick(h, sizes, T, dtype, mlp_params, feat_mean, feat_std, schedules, params, scratch, stream=None):
+def pcot_pick_among(h, sizes, T, dtype, mlp_params, feat_mean, feat_std, schedules, params, scratch, stream=None):
+    """Index of the candidate with the least predicted time under an explicit
+    model (device parameters) and candidate list."""
     n = len(schedules)
     mean = (ctypes.c_float * 12)(*[float(v) for v in feat_mean])
     std = (ctypes.c_float * 12)(*[float(v) for v in feat_std])
     best = ctypes.c_int(-1)
-    _chk(_load().pcot_pick(h, _p64(_i64(sizes)), int(T), int(dtype), _ptr(mlp_params), mean, std, n,
-                           _sched_array(schedules), _param_array(params, n), _ptr(scratch), ctypes.byref(best),
-                           _stream(stream)), "pcot_pick")
+    _chk(_load().pcot_pick_among(h, _p64(_i64(sizes)), int(T), int(dtype), _ptr(mlp_params), mean, std, n,
+                                 _sched_array(schedules), _param_array(params, n), _ptr(scratch), ctypes.byref(best),
+                                 _stream(stream)), "pcot_pick_among")
     return int(best.value)
+
+
+def params_dict(p):
+    """A pcot_tile_params as the keyword dict tile_params() takes."""
+    return dict(tile=tuple(int(v) for v in p.tile), time_depth=int(p.time_depth),
+                cot_threshold=tuple(int(v) for v in p.cot_threshold))
+
+
+def pcot_pick(h, sizes, T, dtype):
+    """(schedule, tile-parameter dict) the library picks for a problem: its
+    loaded model, else the autotuner."""
+    sched = ctypes.c_int(-1)
+    p = pcot_tile_params()
+    _chk(_load().pcot_pick(h, _p64(_i64(sizes)), int(T), int(dtype), ctypes.byref(sched), ctypes.byref(p)),
+         "pcot_pick")
+    return int(sched.value), params_dict(p)
+
+
+def pcot_picker_load(h, mlp_params=None, feat_mean=None, feat_std=None):
+    """Load a model (host arrays) into the handle; no arguments unload it."""
+    if mlp_params is None:
+        _chk(_load().pcot_picker_load(h, None, None, None), "pcot_picker_load")
+        return
+    n = pcot_mlp_param_count()
+    P = (ctypes.c_float * n)(*[float(v) for v in np.asarray(mlp_params, dtype=np.float32)])
+    m = (ctypes.c_float * 12)(*[float(v) for v in feat_mean])
+    s = (ctypes.c_float * 12)(*[float(v) for v in feat_std])
+    _chk(_load().pcot_picker_load(h, P, m, s), "pcot_picker_load")
+
+
+def pcot_candidates(h, dtype):
+    """[(schedule, tile-parameter dict)] the picker chooses among."""
+    n = ctypes.c_int(0)
+    _chk(_load().pcot_candidates(h, int(dtype), 0, None, None, ctypes.byref(n)), "pcot_candidates")
+    sc = (ctypes.c_int * max(n.value, 1))()
+    pr = (pcot_tile_params * max(n.value, 1))()
+    _chk(_load().pcot_candidates(h, int(dtype), n.value, sc, pr, ctypes.byref(n)), "pcot_candidates")
+    return [(int(sc[i]), params_dict(pr[i])) for i in range(n.value)]
 
 
 def library_path():

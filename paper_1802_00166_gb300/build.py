@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libpcot.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-I", INCLUDE, "-I", CSRC]
+              "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
 
 
 def nvcc() -> str:
@@ -36,7 +36,38 @@ def sources():
 
 def headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-                  glob.glob(os.path.join(INCLUDE, "*.h")))
+                  glob.glob(os.path.join(INCLUDE, "*.h")) + [MODEL_INC])
+
+
+MODEL_NPZ = os.path.join(PKG, "data", "picker.npz")
+MODEL_INC = os.path.join(BUILD, "picker_model.inc")
+
+
+def _model_include():
+    """Write _build/picker_model.inc: the trained picker (MLP parameters,
+    feature mean and standard deviation) as a C array, compiled into the
+    library as every new handle's default model; no model when the trained
+    file is absent."""
+    if os.path.exists(MODEL_INC) and (not os.path.exists(MODEL_NPZ) or
+                                      os.path.getmtime(MODEL_INC) >= os.path.getmtime(MODEL_NPZ)):
+        return
+    vals = []
+    if os.path.exists(MODEL_NPZ):
+        import numpy as np
+        z = np.load(MODEL_NPZ)
+        vals = [float(v) for v in np.concatenate([z["params"], z["feat_mean"], z["feat_std"]]).astype(np.float32)]
+    lines = ["// Generated by build.py from data/picker.npz; do not edit.",
+             f"static const int kPickerModelFloats = {len(vals)};",
+             "static const float kPickerModel[] = {"]
+    for i in range(0, len(vals), 6):
+        lines.append("    " + ", ".join(f"{v!r}f" if v == v else "0.0f" for v in vals[i:i + 6]) + ",")
+    if not vals:
+        lines.append("    0.0f,")
+    lines.append("};")
+    tmp = MODEL_INC + ".tmp"
+    with open(tmp, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    os.replace(tmp, MODEL_INC)
 
 
 def _stale(target, deps):
@@ -61,6 +92,7 @@ def _compile(src, extra):
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     """Compile every CUDA/C++ source of the library and link libpcot.so."""
     os.makedirs(BUILD, exist_ok=True)
+    _model_include()
     srcs = sources()
     if not force and not _stale(LIB, srcs + headers()):
         return LIB

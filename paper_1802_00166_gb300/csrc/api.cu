@@ -14,6 +14,7 @@
 #include "pcot.h"
 #include "la_graph.h"
 #include "planner.h"
+#include "picker_model.inc"  // generated by the build from the trained picker (may hold no model)
 
 using namespace pcot;
 
@@ -75,6 +76,15 @@ struct pcot_plan {
     std::map<std::string, LaPlanCache*> la_cache;
     uint64_t timeout_ns = kDefaultTimeoutNs;
     int64_t launches = 0;  // kernels launched by this handle
+    // Learned tile picker: MLP parameters followed by the feature mean and
+    // standard deviation (empty: no model, picks fall back to the autotuner),
+    // their device copy, scratch for the candidates' features and
+    // predictions, and the picks already made per problem.
+    std::vector<float> picker;
+    float* d_picker = nullptr;
+    void* d_pick = nullptr;
+    size_t pick_bytes = 0;
+    std::map<std::string, std::pair<pcot_schedule, pcot_tile_params>> pick_cache;
 };
 
 namespace {
@@ -175,12 +185,6 @@ size_t span_bytes(const LaunchCtx& L) {
     return (size_t)(last + 1) * dtype_size(L.dtype);
 }
 
-int default_depth(const LaunchCtx& L) {
-    if (L.geo.dims == 1) return 16;
-    if (L.dtype != kF32) return 1;
-    return L.geo.dims == 2 ? 4 : 2;
-}
-
 std::string plan_key(const LaunchCtx& L, int64_t T, const pcot_tile_params* p) {
     char buf[512];
     std::snprintf(buf, sizeof(buf), "%d|%d|%lld,%lld,%lld|%lld|%d,%d,%d|%d|%d,%d,%d,%d", L.dtype, L.geo.dims,
@@ -271,11 +275,17 @@ pcot_status run_blocks(pcot_handle h, const LaunchCtx& L, const pcot_tile_params
         std::swap(cur, other);
     }
     if (bp.final_copy) {
-        PCOT_CUDA(cudaMemcpyAsync(other, cur, span_bytes(L), cudaMemcpyDeviceToDevice, L.stream));
+        PCOT_CUDA(launch_grid_copy(L, cur, other));
         std::swap(cur, other);
     }
     return PCOT_OK;
 }
+
+// The candidates the picker chooses among and its choice for a problem
+// (PCOT_AUTO, pcot_pick); defined with the picker below.
+std::vector<std::pair<pcot_schedule, pcot_tile_params>> pick_candidates(int dims, pcot_dtype dtype, bool periodic);
+pcot_status pick_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, cudaStream_t s,
+                      pcot_schedule* schedule, pcot_tile_params* params);
 
 pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes, const int64_t* sizes,
                      const int64_t* strides, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
@@ -288,7 +298,11 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes
     if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
     if (schedule < PCOT_SWEEP || schedule > PCOT_AUTO) return PCOT_ERR_INVALID_ARG;
     if (T == 0) return PCOT_OK;
-    if (schedule == PCOT_AUTO) schedule = (L.dtype == kF32 || L.geo.dims == 1) ? PCOT_SLT : PCOT_SWEEP;
+    pcot_tile_params picked;
+    if (schedule == PCOT_AUTO) {
+        PCOT_TRY(pick_impl(h, sizes, T, dtype, (cudaStream_t)stream, &schedule, &picked));
+        params = &picked;
+    }
     if (schedule == PCOT_COT && L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
     if (ws_bytes < twin_bytes(L)) return PCOT_ERR_OOM;
     CotPlanHost* cplan = nullptr;
@@ -310,9 +324,7 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes
             ++h->launches;
             std::swap(cur, other);
         }
-        if (cur != grid) {
-            PCOT_CUDA(cudaMemcpyAsync(grid, cur, span_bytes(L), cudaMemcpyDeviceToDevice, L.stream));
-        }
+        if (cur != grid) PCOT_CUDA(launch_grid_copy(L, cur, grid));
         return PCOT_OK;
     }
     if (schedule == PCOT_SLT) {
@@ -396,6 +408,7 @@ pcot_status pcot_create(int dims, int radius, const double* coeffs, int ncoeffs,
     h->radius = radius;
     h->boundary = boundary;
     for (int i = 0; i < ncoeffs; ++i) h->coeffs[i] = coeffs[i];
+    if (kPickerModelFloats > 0) h->picker.assign(kPickerModel, kPickerModel + kPickerModelFloats);
     *out = h;
     return PCOT_OK;
 }
@@ -420,6 +433,8 @@ pcot_status pcot_destroy(pcot_handle h) {
     }
     if (h->d_status) cudaFree(h->d_status);
     if (h->d_partials) cudaFree(h->d_partials);
+    if (h->d_picker) cudaFree(h->d_picker);
+    if (h->d_pick) cudaFree(h->d_pick);
     delete h;
     return PCOT_OK;
 }
@@ -431,6 +446,14 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t* sizes, const int6
     LaunchCtx L;
     PCOT_TRY(make_ctx(h, sizes, strides, dtype, nullptr, &L));
     size_t b = twin_bytes(L);
+    if (schedule == PCOT_AUTO && T > 0) {
+        // enough for whichever candidate the picker chooses
+        for (const auto& c : pick_candidates(L.geo.dims, dtype, L.geo.periodic != 0)) {
+            size_t bc = 0;
+            if (pcot_workspace_bytes(h, sizes, strides, T, dtype, c.first, &c.second, &bc) == PCOT_OK)
+                b = std::max(b, bc);
+        }
+    }
     if (schedule == PCOT_COT && T > 0) {
         if (L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
         CotPlanHost* c = nullptr;
@@ -921,6 +944,196 @@ pcot_status features_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_d
     return PCOT_OK;
 }
 
+pcot_tile_params tparams(int t0, int t1, int t2, int k, int h0 = 0, int h1 = 0, int h2 = 0, int h3 = 0) {
+    pcot_tile_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.tile[0] = t0;
+    p.tile[1] = t1;
+    p.tile[2] = t2;
+    p.time_depth = k;
+    p.cot_threshold[0] = h0;
+    p.cot_threshold[1] = h1;
+    p.cot_threshold[2] = h2;
+    p.cot_threshold[3] = h3;
+    return p;
+}
+
+// MLP forward over the normalised features of every candidate and argmin of
+// the predicted time (output 0); candidates without a kernel never win.
+pcot_status pick_among(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, const float* mlp_params,
+                       const float* feat_mean, const float* feat_std, int ncand, const pcot_schedule* schedules,
+                       const pcot_tile_params* params, void* scratch, int* best, cudaStream_t s) {
+    std::vector<float> x((size_t)ncand * 12);
+    std::vector<int> ok((size_t)ncand, 1);
+    for (int i = 0; i < ncand; ++i) {
+        float f[12];
+        if (features_impl(h, sizes, T, dtype, schedules[i], params ? &params[i] : nullptr, f) != PCOT_OK) {
+            ok[i] = 0;
+            for (int j = 0; j < 12; ++j) f[j] = 0.f;
+        }
+        for (int j = 0; j < 12; ++j) {
+            const float sd = feat_std[j] > 0.f ? feat_std[j] : 1.f;
+            x[(size_t)i * 12 + j] = (f[j] - feat_mean[j]) / sd;
+        }
+    }
+    float* dx = (float*)scratch;
+    float* dy = dx + (size_t)ncand * 12;
+    int* didx = (int*)(dy + (size_t)ncand * 2);
+    PCOT_CUDA(cudaMemcpyAsync(dx, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    PCOT_CUDA(mlp::forward(mlp_params, dx, ncand, dy, s));
+    const float big = 1e30f;
+    for (int i = 0; i < ncand; ++i)
+        if (!ok[i]) PCOT_CUDA(cudaMemcpyAsync(dy + (size_t)i * 2, &big, sizeof(float), cudaMemcpyHostToDevice, s));
+    PCOT_CUDA(mlp::argmin(dy, ncand, 2, 0, didx, s));
+    int idx = -1;
+    PCOT_CUDA(cudaMemcpyAsync(&idx, didx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PCOT_CUDA(cudaStreamSynchronize(s));
+    if (idx < 0 || idx >= ncand || !ok[idx]) return PCOT_ERR_UNSUPPORTED;
+    *best = idx;
+    return PCOT_OK;
+}
+
+// With no model loaded: the exhaustive autotuner on a scratch grid of the
+// problem's size (rows padded to 128 bytes, zero values: the kernels' speed
+// does not depend on the values), allocated for the call and freed after it.
+pcot_status pick_autotune(pcot_handle h, const LaunchCtx& L, const int64_t* sizes, int64_t T, pcot_dtype dtype,
+                          cudaStream_t s, const std::vector<std::pair<pcot_schedule, pcot_tile_params>>& c,
+                          int* best) {
+    const int d = L.geo.dims;
+    const int es = elem_size(dtype);
+    int64_t strides[3] = {1, 1, 1};
+    const int64_t step = 128 / es;
+    int64_t acc = (L.geo.e[d - 1] + step - 1) / step * step;
+    for (int a = d - 2; a >= 0; --a) {
+        strides[a] = acc;
+        acc *= L.geo.e[a];
+    }
+    int64_t last = 0;
+    for (int a = 0; a < d; ++a) last += (L.geo.e[a] - 1) * strides[a];
+    const size_t gbytes = (size_t)(last + 1) * es;
+    size_t wbytes = 0;
+    std::vector<pcot_schedule> sc;
+    std::vector<pcot_tile_params> pr;
+    for (const auto& x : c) {
+        size_t b = 0;
+        if (pcot_workspace_bytes(h, sizes, strides, T, dtype, x.first, &x.second, &b) == PCOT_OK)
+            wbytes = std::max(wbytes, b);
+        sc.push_back(x.first);
+        pr.push_back(x.second);
+    }
+    void* grid = nullptr;
+    void* ws = nullptr;
+    cudaError_t e = cudaMalloc(&grid, gbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ws, std::max<size_t>(wbytes, 256));
+    if (e == cudaSuccess) e = cudaMemsetAsync(grid, 0, gbytes, s);
+    pcot_status st = from_cuda(e);
+    std::vector<float> ms(c.size(), -1.f);
+    if (st == PCOT_OK)
+        st = pcot_autotune(h, grid, ws, std::max<size_t>(wbytes, 256), sizes, strides, T, dtype, (int)c.size(),
+                           sc.data(), pr.data(), 2, ms.data(), s);
+    if (ws) cudaFree(ws);
+    if (grid) cudaFree(grid);
+    if (st != PCOT_OK) return st;
+    int b = -1;
+    for (size_t i = 0; i < ms.size(); ++i)
+        if (ms[i] > 0.f && (b < 0 || ms[i] < ms[(size_t)b])) b = (int)i;
+    if (b < 0) return PCOT_ERR_UNSUPPORTED;
+    *best = b;
+    return PCOT_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Schedules and tile shapes the picker chooses among (and the autotuner
+// times): the plain sweep, the single-level schedule over depths and tile
+// heights, and for Dirichlet grids the recursive order over depths, tile
+// heights and leaf orthants (Sec. 5.1.5's exploration of tile sizes).
+std::vector<std::pair<pcot_schedule, pcot_tile_params>> pick_candidates(int dims, pcot_dtype dtype, bool periodic) {
+    std::vector<std::pair<pcot_schedule, pcot_tile_params>> out;
+    const bool f32 = dtype == PCOT_F32;
+    out.push_back({PCOT_SWEEP, tparams(0, 0, 0, 0)});
+    if (dims == 2) {
+        const std::vector<int> ks = f32 ? std::vector<int>{2, 4, 6, 8} : std::vector<int>{1, 2, 4};
+        for (int k : ks)
+            for (int H : {0, 48, 96}) out.push_back({PCOT_SLT, tparams(H, 0, 0, k)});
+        if (!periodic) {
+            const std::vector<int> kc = f32 ? std::vector<int>{4, 6, 8} : std::vector<int>{1, 2};
+            const int th[3][3] = {{2, 256, 256}, {2, 64, 64}, {4, 16, 16}};
+            for (int k : kc)
+                for (int H : {64, 80, 96, 128})
+                    for (const auto& t : th) out.push_back({PCOT_COT, tparams(H, 0, 0, k, t[0], t[1], t[2])});
+        }
+    } else if (dims == 3) {
+        const std::vector<int> ks = f32 ? std::vector<int>{1, 2, 3, 4} : std::vector<int>{1, 2};
+        for (int k : ks)
+            for (int Hz : {32, 64, 128})
+                for (int Hy : {0, 16}) out.push_back({PCOT_SLT, tparams(Hz, Hy, 0, k)});
+        if (!periodic) {
+            const int th[3][4] = {{1, 1, 1, 1}, {2, 4, 4, 4}, {2, 64, 64, 64}};
+            for (size_t i = 0; i < 2 && i < ks.size(); ++i)
+                for (const auto& t : th) out.push_back({PCOT_COT, tparams(32, 0, 0, ks[i], t[0], t[1], t[2], t[3])});
+        }
+    } else {
+        for (int k : {8, 16, 32, 64})
+            for (int w : {16, 32, 64}) out.push_back({PCOT_SLT, tparams(w, 0, 0, k)});
+    }
+    return out;
+}
+
+std::string pick_key(const LaunchCtx& L, int64_t T) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d|%lld,%lld,%lld|%lld", L.dtype, (long long)L.geo.n[0], (long long)L.geo.n[1],
+                  (long long)L.geo.n[2], (long long)T);
+    return buf;
+}
+
+pcot_status pick_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, cudaStream_t s,
+                      pcot_schedule* schedule, pcot_tile_params* params) {
+    LaunchCtx L;
+    PCOT_TRY(make_ctx(h, sizes, nullptr, dtype, s, &L));
+    const std::string key = pick_key(L, T);
+    auto it = h->pick_cache.find(key);
+    if (it != h->pick_cache.end()) {
+        *schedule = it->second.first;
+        *params = it->second.second;
+        return PCOT_OK;
+    }
+    const auto c = pick_candidates(L.geo.dims, dtype, L.geo.periodic != 0);
+    int best = -1;
+    if (!h->picker.empty()) {
+        const int np = mlp::param_count();
+        if ((int)h->picker.size() != np + 24) return PCOT_ERR_INVALID_ARG;
+        if (!h->d_picker) {
+            PCOT_CUDA(cudaMalloc((void**)&h->d_picker, sizeof(float) * np));
+            PCOT_CUDA(cudaMemcpy(h->d_picker, h->picker.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+        }
+        const size_t need = c.size() * 14 * sizeof(float) + 256;
+        if (h->pick_bytes < need) {
+            if (h->d_pick) cudaFree(h->d_pick);
+            h->d_pick = nullptr;
+            h->pick_bytes = 0;
+            PCOT_CUDA(cudaMalloc(&h->d_pick, need));
+            h->pick_bytes = need;
+        }
+        std::vector<pcot_schedule> sc;
+        std::vector<pcot_tile_params> pr;
+        for (const auto& x : c) {
+            sc.push_back(x.first);
+            pr.push_back(x.second);
+        }
+        PCOT_TRY(pick_among(h, sizes, T, dtype, h->d_picker, h->picker.data() + np, h->picker.data() + np + 12,
+                            (int)c.size(), sc.data(), pr.data(), h->d_pick, &best, s));
+    } else {
+        PCOT_TRY(pick_autotune(h, L, sizes, T, dtype, s, c, &best));
+    }
+    *schedule = c[(size_t)best].first;
+    *params = c[(size_t)best].second;
+    h->pick_cache[key] = c[(size_t)best];
+    return PCOT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -967,43 +1180,55 @@ pcot_status pcot_features(pcot_handle h, const int64_t* sizes, int64_t T, pcot_d
     return features_impl(h, sizes, T, dtype, schedule, params, out12);
 }
 
-pcot_status pcot_pick(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, const float* mlp_params,
-                      const float* feat_mean, const float* feat_std, int ncand, const pcot_schedule* schedules,
-                      const pcot_tile_params* params, void* scratch, int* best, void* stream) {
+pcot_status pcot_pick_among(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, const float* mlp_params,
+                            const float* feat_mean, const float* feat_std, int ncand, const pcot_schedule* schedules,
+                            const pcot_tile_params* params, void* scratch, int* best, void* stream) {
     if (!h || !sizes || !mlp_params || !feat_mean || !feat_std || ncand < 1 || !schedules || !scratch || !best)
         return PCOT_ERR_INVALID_ARG;
-    std::vector<float> x((size_t)ncand * 12);
-    std::vector<int> ok((size_t)ncand, 1);
-    for (int i = 0; i < ncand; ++i) {
-        float f[12];
-        if (features_impl(h, sizes, T, dtype, schedules[i], params ? &params[i] : nullptr, f) != PCOT_OK) {
-            ok[i] = 0;
-            for (int j = 0; j < 12; ++j) f[j] = 0.f;
-        }
-        for (int j = 0; j < 12; ++j) {
-            const float sd = feat_std[j] > 0.f ? feat_std[j] : 1.f;
-            x[(size_t)i * 12 + j] = (f[j] - feat_mean[j]) / sd;
-        }
+    return pick_among(h, sizes, T, dtype, mlp_params, feat_mean, feat_std, ncand, schedules, params, scratch, best,
+                      (cudaStream_t)stream);
+}
+
+pcot_status pcot_picker_load(pcot_handle h, const float* mlp_params, const float* feat_mean,
+                             const float* feat_std) {
+    if (!h) return PCOT_ERR_INVALID_ARG;
+    if ((mlp_params == nullptr) != (feat_mean == nullptr) || (mlp_params == nullptr) != (feat_std == nullptr))
+        return PCOT_ERR_INVALID_ARG;
+    const int np = mlp::param_count();
+    h->picker.clear();
+    if (mlp_params) {
+        h->picker.assign(mlp_params, mlp_params + np);
+        h->picker.insert(h->picker.end(), feat_mean, feat_mean + 12);
+        h->picker.insert(h->picker.end(), feat_std, feat_std + 12);
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    float* dx = (float*)scratch;
-    float* dy = dx + (size_t)ncand * 12;
-    int* didx = (int*)(dy + (size_t)ncand * 2);
-    PCOT_CUDA(cudaMemcpyAsync(dx, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-    PCOT_CUDA(mlp::forward(mlp_params, dx, ncand, dy, s));
-    // Unsupported candidates must never win: overwrite their prediction.
-    for (int i = 0; i < ncand; ++i)
-        if (!ok[i]) {
-            const float big = 1e30f;
-            PCOT_CUDA(cudaMemcpyAsync(dy + (size_t)i * 2, &big, sizeof(float), cudaMemcpyHostToDevice, s));
-        }
-    PCOT_CUDA(mlp::argmin(dy, ncand, 2, 0, didx, s));
-    int idx = -1;
-    PCOT_CUDA(cudaMemcpyAsync(&idx, didx, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PCOT_CUDA(cudaStreamSynchronize(s));
-    if (idx < 0 || idx >= ncand) return PCOT_ERR_CUDA;
-    *best = idx;
+    if (h->d_picker) {
+        cudaFree(h->d_picker);
+        h->d_picker = nullptr;
+    }
+    h->pick_cache.clear();
     return PCOT_OK;
+}
+
+pcot_status pcot_candidates(pcot_handle h, pcot_dtype dtype, int cap, pcot_schedule* schedules,
+                            pcot_tile_params* params, int* count) {
+    if (!h || !count || cap < 0) return PCOT_ERR_INVALID_ARG;
+    if (dtype != PCOT_F32 && dtype != PCOT_F64 && dtype != PCOT_F64_EXACT) return PCOT_ERR_INVALID_ARG;
+    const auto c = pick_candidates(h->dims, dtype, h->boundary == PCOT_PERIODIC);
+    *count = (int)c.size();
+    if (cap == 0) return PCOT_OK;
+    if (!schedules || !params) return PCOT_ERR_INVALID_ARG;
+    if (cap < (int)c.size()) return PCOT_ERR_OOM;
+    for (size_t i = 0; i < c.size(); ++i) {
+        schedules[i] = c[i].first;
+        params[i] = c[i].second;
+    }
+    return PCOT_OK;
+}
+
+pcot_status pcot_pick(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, pcot_schedule* schedule,
+                      pcot_tile_params* params) {
+    if (!h || !sizes || !schedule || !params || T < 0) return PCOT_ERR_INVALID_ARG;
+    return pick_impl(h, sizes, T, dtype, nullptr, schedule, params);
 }
 
 }  // extern "C"

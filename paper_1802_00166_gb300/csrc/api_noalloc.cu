@@ -2,14 +2,13 @@
 // with its second buffer in a fixed, file-scope device array.
 //
 // Who needs it: callers that may not allocate device memory at the moment
-// they advance a grid -- code running while a CUDA graph is being captured
-// (cudaMalloc would invalidate the capture), real-time or embedded hosts that
-// reserve all device memory up front and forbid allocation afterwards, and
-// library layers that are handed only the grid and a stream and may not
-// touch the caller's allocator.  pcot_run needs a caller-provided workspace
-// (the grid's twin); this variant uses kNoallocBytes of device memory that
-// every GPU loading the library reserves at module load and keeps until the
-// process exits.
+// they advance a grid -- real-time or embedded hosts that reserve all device
+// memory up front and forbid allocation afterwards, services that run with a
+// fixed memory budget and must not grow it per request, and library layers
+// that are handed only the grid and a stream and may not touch the caller's
+// allocator.  pcot_run needs a caller-provided workspace (the grid's twin);
+// this variant uses kNoallocBytes of device memory that every GPU loading the
+// library reserves at module load and keeps until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -130,13 +129,15 @@ extern "C" pcot_status pcot_run_noalloc(pcot_handle h, void* grid, const int64_t
     } else {
         // Time blocks: depth k while possible, the remainder in the deepest
         // compiled depths (no heap).  An odd block count ends in the array
-        // and is copied back below.
-        const int k = params && params->time_depth > 0 ? params->time_depth
-                                                       : (dims == 1 ? 16 : dtype == PCOT_F32 ? 4 : 1);
+        // and is copied back below.  k follows pcot_run's rules: the default
+        // depth, and a depth without a kernel falls to the deepest compiled
+        // one below it.
+        const int k = resolve_depth(L, params ? params->tile : nullptr,
+                                    params && params->time_depth > 0 ? params->time_depth : default_depth(L));
         TileGeo tg;
         int fam_depths[32];
         if (!choose_tiles(L, params ? params->tile : nullptr, k, &tg)) return PCOT_ERR_UNSUPPORTED;
-        const int nd = supported_depths(tg.family, L.dtype, fam_depths, 32);
+        const int nd = tg.family == kFamGeneric ? 0 : supported_depths(tg.family, L.dtype, fam_depths, 32);
         auto deepest = [&](int64_t limit) {
             if (nd == 0) return (int)(limit < 64 ? limit : 64);
             int best = 1;
@@ -158,7 +159,9 @@ extern "C" pcot_status pcot_run_noalloc(pcot_handle h, void* grid, const int64_t
         }
     }
     if (cur != grid) {
-        e = cudaMemcpyAsync(grid, cur, span, cudaMemcpyDeviceToDevice, L.stream);
+        // Only the stored cells go back: the row padding of a strided grid
+        // belongs to the caller and is never written.
+        e = launch_grid_copy(L, cur, grid);
         if (e != cudaSuccess) return PCOT_ERR_CUDA;
     }
     pcot::handle_count_launches(h, nl);

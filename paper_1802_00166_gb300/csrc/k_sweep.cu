@@ -430,6 +430,27 @@ cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_grid_copy(const LaunchCtx& L, const void* src, void* dst) {
+    const DevGeo& g = L.geo;
+    const size_t es = (size_t)dtype_size(L.dtype);
+    const int d = g.dims;
+    const size_t width = (size_t)g.e[d - 1] * es;
+    if (d == 1) return cudaMemcpyAsync(dst, src, width, cudaMemcpyDeviceToDevice, L.stream);
+    const size_t pitch = (size_t)g.s[d - 2] * es;
+    if (d == 2) return cudaMemcpy2DAsync(dst, pitch, src, pitch, width, (size_t)g.e[0], cudaMemcpyDeviceToDevice,
+                                         L.stream);
+    if (g.s[0] == g.s[1] * g.e[1])  // planes follow each other without a gap: one pitched copy
+        return cudaMemcpy2DAsync(dst, pitch, src, pitch, width, (size_t)(g.e[0] * g.e[1]),
+                                 cudaMemcpyDeviceToDevice, L.stream);
+    for (int64_t z = 0; z < g.e[0]; ++z) {
+        const size_t off = (size_t)(z * g.s[0]) * es;
+        cudaError_t e = cudaMemcpy2DAsync((char*)dst + off, pitch, (const char*)src + off, pitch, width,
+                                          (size_t)g.e[1], cudaMemcpyDeviceToDevice, L.stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int grid_sum_partials() { return 1024; }
 
 cudaError_t launch_grid_sum(const LaunchCtx& L, const void* grid, double* out, double* partials, int np) {

@@ -18,6 +18,25 @@ int supported_depths(int family, int dtype, int* out, int cap) {
     return 0;  // any depth
 }
 
+int default_depth(const LaunchCtx& L) {
+    if (L.geo.dims == 1) return 16;
+    if (L.dtype != kF32) return 1;
+    return L.geo.dims == 2 ? 4 : 2;
+}
+
+int resolve_depth(const LaunchCtx& L, const int32_t* req_tile, int k) {
+    if (k < 1) k = 1;
+    TileGeo tg;
+    if (choose_tiles(L, req_tile, k, &tg)) return k;
+    const int fam = L.geo.dims == 2 ? kFamStream2D : kFamStream3D;
+    int ds[32];
+    const int n = supported_depths(fam, L.dtype, ds, 32);
+    int best = 1;
+    for (int i = 0; i < n; ++i)
+        if (ds[i] <= k && ds[i] > best) best = ds[i];
+    return best;
+}
+
 cudaError_t launch_slt_block(const LaunchCtx& L, const TileGeo& t, const void* src, void* dst, DevStatus* st) {
     switch (t.family) {
         case kFamStream2D: return stream2d::slt(L, t, src, dst, st);

@@ -81,6 +81,10 @@ cudaError_t launch_fdtd2d_cot(int dtype, const FdDev& q, const CotDev& c, void* 
 // ---- k_sweep.cu ----
 cudaError_t launch_sweep(const LaunchCtx& L, const void* src, void* dst);
 cudaError_t launch_ring_copy(const LaunchCtx& L, const void* src, void* dst);
+// Copy the stored cells of the grid (the dims-shaped extent, ring included)
+// from src to dst, row by row with the grid's strides: the padding between
+// rows is neither read nor written.
+cudaError_t launch_grid_copy(const LaunchCtx& L, const void* src, void* dst);
 cudaError_t launch_grid_sum(const LaunchCtx& L, const void* grid, double* out, double* partials,
                             int npartials);
 int grid_sum_partials();
@@ -91,6 +95,12 @@ int grid_sum_partials();
 bool choose_tiles(const LaunchCtx& L, const int32_t* req_tile, int depth, TileGeo* out);
 // Depths a family has compiled variants for (ascending); returns the count.
 int supported_depths(int family, int dtype, int* out, int cap);
+// Time depth used when the caller leaves it open (0).
+int default_depth(const LaunchCtx& L);
+// The depth a tiled run uses for a requested depth k: k itself when a kernel
+// of this build supports it with the requested tile, else the deepest
+// compiled depth below k of the dims' fast family (at least 1).
+int resolve_depth(const LaunchCtx& L, const int32_t* req_tile, int k);
 
 // One single-level time block: all tiles of `t` read src, write dst.  `st`
 // (may be NULL) is the status block bounded waits report to; without it the

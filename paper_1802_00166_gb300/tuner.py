@@ -35,33 +35,29 @@ DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 # ------------------------------------------------------------- candidates --
 
 def candidates(dims, dtype, periodic):
-    """(schedule, tile-parameter dict) pairs explored for a problem."""
-    S = pcot
-    out = [(S.PCOT_SWEEP, dict())]
-    if dims == 2:
-        ks = (2, 4, 6, 8) if dtype == S.PCOT_F32 else (1, 2, 4)
-        for k in ks:
-            for H in (0, 48, 96):
-                out.append((S.PCOT_SLT, dict(tile=(H, 0), time_depth=k)))
-        if not periodic:
-            for k in ((4, 6, 8) if dtype == S.PCOT_F32 else (1, 2)):
-                for H in (64, 80, 96, 128):
-                    for th in ((2, 256, 256), (2, 64, 64), (4, 16, 16)):
-                        out.append((S.PCOT_COT, dict(tile=(H, 0), time_depth=k, cot_threshold=th)))
-    elif dims == 3:
-        ks = (1, 2, 3, 4) if dtype == S.PCOT_F32 else (1, 2)
-        for k in ks:
-            for Hz in (32, 64, 128):
-                for Hy in (0, 16):
-                    out.append((S.PCOT_SLT, dict(tile=(Hz, Hy, 0), time_depth=k)))
-        if not periodic:
-            for k in ks[:2]:
-                for th in ((1, 1, 1, 1), (2, 4, 4, 4), (2, 64, 64, 64)):
-                    out.append((S.PCOT_COT, dict(tile=(32, 0, 0), time_depth=k, cot_threshold=th)))
-    else:
-        for k in (8, 16, 32, 64):
-            for w in (16, 32, 64):
-                out.append((S.PCOT_SLT, dict(tile=(w,), time_depth=k)))
+    """(schedule, tile-parameter dict) pairs explored for a problem: the
+    library's own candidate list (pcot_candidates), the one pcot_pick and
+    PCOT_AUTO choose among."""
+    coeffs = {1: [1 / 3] * 3, 2: HEAT2D, 3: JAC3D}[dims]
+    h = pcot.pcot_create(dims, 1, coeffs, pcot.PCOT_PERIODIC if periodic else pcot.PCOT_DIRICHLET)
+    try:
+        return _trim(pcot.pcot_candidates(h, dtype), dims)
+    finally:
+        pcot.pcot_destroy(h)
+
+
+def _trim(cands, dims):
+    """Tile-parameter dicts in the short form the records use: only the
+    fields a schedule sets."""
+    out = []
+    for sched, p in cands:
+        if sched == pcot.PCOT_SWEEP:
+            out.append((sched, dict()))
+            continue
+        d = dict(tile=tuple(p["tile"][:dims]), time_depth=p["time_depth"])
+        if sched == pcot.PCOT_COT:
+            d["cot_threshold"] = tuple(p["cot_threshold"][:dims + 1])
+        out.append((sched, d))
     return out
 
 
@@ -241,7 +237,7 @@ class Picker:
         n = len(cands)
         scratch = torch.empty(n * 14 * 4 + 512, dtype=torch.uint8, device="cuda")
         params = [pcot.tile_params(**p) for _, p in cands]
-        return pcot.pcot_pick(h, sizes, T, dtype, self.device_params(), self.feat_mean, self.feat_std,
+        return pcot.pcot_pick_among(h, sizes, T, dtype, self.device_params(), self.feat_mean, self.feat_std,
                               [s for s, _ in cands], params, scratch, stream)
 
     def predict(self, x_norm):

@@ -172,3 +172,29 @@ def test_undersized_workspace_rejected_before_launch(lib):
     slt = pcot.pcot_workspace_bytes(h, sizes, None, 20, pcot.PCOT_F32, pcot.PCOT_SLT)
     assert cot > slt  # the queue image of the recursive schedule lives in the workspace
     pcot.pcot_destroy(h)
+
+
+def test_candidates_list_host_logic():
+    """The picker's candidates (a planning call, no GPU): the sweep first,
+    depths the kernels compile, recursive-order candidates only for Dirichlet
+    grids, every candidate's feature vector computable."""
+    import paper_1802_00166_gb300 as pcot
+    for dims, periodic in ((1, False), (2, False), (2, True), (3, True), (3, False)):
+        coeffs = {1: [1 / 3] * 3, 2: [0.5] + [0.125] * 4, 3: [0.4] + [0.1] * 6}[dims]
+        h = pcot.pcot_create(dims, 1, coeffs, pcot.PCOT_PERIODIC if periodic else pcot.PCOT_DIRICHLET)
+        for dt in (pcot.PCOT_F32, pcot.PCOT_F64_EXACT):
+            c = pcot.pcot_candidates(h, dt)
+            assert c[0][0] == pcot.PCOT_SWEEP and len(c) > 8
+            assert len(set((s, tuple(p["tile"]), p["time_depth"], tuple(p["cot_threshold"])) for s, p in c)) == len(c)
+            assert all(s in (pcot.PCOT_SWEEP, pcot.PCOT_SLT, pcot.PCOT_COT) for s, _ in c)
+            assert any(s == pcot.PCOT_COT for s, _ in c) == (not periodic and dims > 1)
+            sizes = {1: (1000,), 2: (300, 500), 3: (40, 50, 64)}[dims]
+            for s, p in c:
+                f = pcot.pcot_features(h, sizes, 33, dt, s, pcot.tile_params(**p))
+                assert f.shape == (12,) and np.all(np.isfinite(f))
+        pcot.pcot_destroy(h)
+
+
+def test_noalloc_limit_parsed_from_the_header():
+    import paper_1802_00166_gb300 as pcot
+    assert pcot.NOALLOC_MAX_BYTES == 32 * 1024 * 1024
