@@ -40,11 +40,10 @@ struct Shape {
     static constexpr int Wo = 32 * E - 2 * Kp;
 };
 
-// FP32 FMA-mode tiles of depth 3 and 4 update a lane's two cells with packed
-// f32x2 instructions (+1-4% there; at depths 1 and 2 the pair assembly cost
-// more than it saved, -3%).
+// FP32 FMA-mode tiles update a lane's two cells with packed f32x2
+// instructions.
 template <class T, bool EXACT, int K>
-constexpr bool kPacked3 = std::is_same<T, float>::value && !EXACT && K >= 3;
+constexpr bool kPacked3 = std::is_same<T, float>::value && !EXACT;
 
 // Register budget per thread: the stage rings hold 3*K*RY*E values.
 template <class T, int K>
@@ -225,18 +224,23 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                 const T wl = __shfl_up_sync(kFull, R[s][SB][r][1], 1);
                 const T er = __shfl_down_sync(kFull, R[s][SB][r][0], 1);
                 if constexpr (kPacked3<T, EXACT, K>) {
-                    // the lane's two cells as one f32x2 pair, same operations and
-                    // order per cell as upd3's FMA mode (bitwise equal)
+                    // the lane's two cells (c0, c1) as one f32x2 pair, same
+                    // operations and order per cell as upd3's FMA mode
+                    // (bitwise equal); the x-neighbours (c-1, c0) and (c1, c2)
+                    // are shifted by one cell, so they enter as scalar FMAs
+                    // on the pair's halves instead of being assembled into
+                    // register pairs
                     const float2 k0 = make_float2(c.c[0], c.c[0]), k1 = make_float2(c.c[1], c.c[1]);
                     const float2 k2 = make_float2(c.c[2], c.c[2]), k3 = make_float2(c.c[3], c.c[3]);
-                    const float2 k4 = make_float2(c.c[4], c.c[4]), k5 = make_float2(c.c[5], c.c[5]);
-                    const float2 k6 = make_float2(c.c[6], c.c[6]);
+                    const float2 k4 = make_float2(c.c[4], c.c[4]);
                     float2 a = __fmul2_rn(k0, make_float2(R[s][SB][r][0], R[s][SB][r][1]));
                     a = __ffma2_rn(k1, make_float2(R[s][SA][r][0], R[s][SA][r][1]), a);
                     a = __ffma2_rn(k3, make_float2(n0, n1), a);
                     a = __ffma2_rn(k4, make_float2(s0, s1), a);
-                    a = __ffma2_rn(k5, make_float2(wl, R[s][SB][r][0]), a);      // west of (c0, c1)
-                    a = __ffma2_rn(k6, make_float2(R[s][SB][r][1], er), a);      // east of (c0, c1)
+                    a.x = __fmaf_rn(c.c[5], wl, a.x);
+                    a.y = __fmaf_rn(c.c[5], R[s][SB][r][0], a.y);
+                    a.x = __fmaf_rn(c.c[6], R[s][SB][r][1], a.x);
+                    a.y = __fmaf_rn(c.c[6], er, a.y);
                     a = __ffma2_rn(k2, make_float2(R[s][SN][r][0], R[s][SN][r][1]), a);
                     out[r][0] = a.x;
                     out[r][1] = a.y;
