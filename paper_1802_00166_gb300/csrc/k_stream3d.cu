@@ -179,6 +179,24 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                 for (int j = 0; j < E; ++j) R[s][u][r][j] = T(0);
 
     const int64_t zbeg = z0 - K, zend = z0 + Hz + K;
+    // Stores: plane zi - K is written for zi in [zs_lo, zs_hi) (the tile's
+    // planes inside the grid's interior); per row, a lane either stores its
+    // two cells as one vector (sfast) or, on a ragged or unaligned edge, cell
+    // by cell (sslow) -- decided once per tile, not per plane.
+    int64_t zs_lo = z0 + K, zs_hi = z0 + Hz + K;
+    if (per) {
+        zs_hi = zs_hi < nz + K ? zs_hi : nz + K;
+    } else {
+        zs_lo = zs_lo > 1 + K ? zs_lo : 1 + K;
+        zs_hi = zs_hi < nz + 1 + K ? zs_hi : nz + 1 + K;
+    }
+    bool any_stx = false;
+#pragma unroll
+    for (int j = 0; j < E; ++j) any_stx = any_stx || stx[j];
+    bool sfast[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) sfast[r] = ystore[r] && svec;
+    const bool sslow = !svec && any_stx;
     T pf[RY][E];
     load_plane(zbeg, pf);
     int buf = 0;
@@ -269,24 +287,23 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                 }
             }
         }
-        const int64_t zo = zi - K;
-        const bool zok = zo >= z0 && zo < z0 + Hz && (per ? zo < nz : (zo >= 1 && zo <= nz));
-        if (zok) {
-            T* const plane = dst + zo * Pz;
+        if (zi >= zs_lo && zi < zs_hi) {
+            T* const plane = dst + (zi - K) * Pz;
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
-                if (!ystore[r]) continue;
-                T* const cell = plane + soff[r];
-                if (svec) {
+                if (sfast[r]) {
                     V q;
                     q.x = out[r][0];
                     q.y = out[r][1];
-                    *reinterpret_cast<V*>(cell) = q;
-                } else {
+                    *reinterpret_cast<V*>(plane + soff[r]) = q;
+                }
+            }
+            if (sslow) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
 #pragma unroll
                     for (int j = 0; j < E; ++j)
-                        if (stx[j]) cell[j] = out[r][j];
-                }
+                        if (ystore[r] && stx[j]) plane[soff[r] + j] = out[r][j];
             }
         }
         buf ^= 1;
