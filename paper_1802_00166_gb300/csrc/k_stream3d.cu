@@ -131,7 +131,14 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         soff[r] = (ybase + r) * Py + xl;
     }
 
-    // The brick's rows of input plane zi (plane index and bounds once per plane).
+    // The brick's rows of input plane zi (plane index and bounds once per
+    // plane).  Per row a lane loads its two cells as one vector (lfast) or,
+    // next to a wrap-around or the grid's edge and on unaligned layouts, cell
+    // by cell (lslow) -- decided once per tile.
+    bool lfast[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) lfast[r] = yin[r] && lvec;
+    const bool lslow = !lvec;
     auto load_plane = [&](int64_t zi, T (&v)[RY][E]) {
         int64_t zs;
         bool zin;
@@ -145,20 +152,21 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
         const T* plane = src + zs * Pz;
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
-            if (!zin || !yin[r]) {
-                v[r][0] = T(0);
-                v[r][1] = T(0);
-                continue;
-            }
-            if (lvec) {
+            if (zin && lfast[r]) {
                 const V q = gload<CG>(reinterpret_cast<const V*>(plane + loff[r]));
                 v[r][0] = q.x;
                 v[r][1] = q.y;
             } else {
-                const T* rowp = plane + yoff[r];
-#pragma unroll
-                for (int j = 0; j < E; ++j) v[r][j] = inb[j] ? gload<CG>(rowp + col[j]) : T(0);
+                v[r][0] = T(0);
+                v[r][1] = T(0);
             }
+        }
+        if (lslow) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    if (zin && yin[r] && inb[j]) v[r][j] = gload<CG>(plane + yoff[r] + col[j]);
         }
     };
 
