@@ -284,7 +284,9 @@ pcot_status pcot_autotune(pcot_handle h, void *grid, void *workspace, size_t wor
  * Learned tile picker.  A 12-64-64-64-2 ReLU MLP (FP32, 9282 parameters in
  * one flat array: W1 (64x12, row = output), b1, W2 (64x64), b2, W3, b3,
  * W4 (2x64), b4) maps a normalised feature vector of (problem, schedule,
- * tile parameters) to (log milliseconds, log modelled HBM bytes).  Training
+ * tile parameters) to two measured quantities, normalised: the log
+ * milliseconds of a run and the log slowdown against the fastest candidate
+ * of the same problem (capped at log 3).  Picks minimise the second.  Training
  * and inference run in the library's kernels; all pointers are DEVICE
  * pointers unless stated.  x is batch x 12, y and targets batch x 2, all
  * row-major.
@@ -311,7 +313,8 @@ pcot_status pcot_mlp_argmin(const float *y, int n, int stride, int col, int *out
 
 /*
  * Feature vector (12 floats, HOST) of one candidate, before normalisation:
- * [dims, radius, log2 n_0, log2 n_1, log2 n_2 (0 when absent), log2 T,
+ * [dims, log2 of the tiles per time block (0 for the sweep), log2 n_0,
+ *  log2 n_1, log2 n_2 (0 when absent), log2 T,
  *  log2 tile_0, log2 tile_1, log2 tile_2 (extents actually used; the grid
  *  extents for the sweep), log2 k (0 for the sweep), log2 of the leaf
  *  orthant volume in tiles (PCOT_COT) or -1 (sweep / single-level), dtype].
@@ -345,9 +348,9 @@ pcot_status pcot_picker_load(pcot_handle h, const float *mlp_params, const float
 
 /*
  * Schedule and tile parameters for a problem (sizes, T, dtype).  With a
- * model loaded: the MLP predicts the time of every candidate of
- * pcot_candidates (forward and argmin kernels on the legacy default stream)
- * and the fastest predicted one is returned.  Without a model: the
+ * model loaded: the MLP predicts every candidate of pcot_candidates
+ * (forward and argmin kernels on the legacy default stream) and the one with
+ * the least predicted slowdown is returned.  Without a model: the
  * exhaustive autotuner (pcot_autotune, two timed runs per candidate) runs on
  * a scratch grid of the problem's size with rows padded to 128 bytes, which
  * the call allocates and frees; the fastest measured candidate is returned.
@@ -360,9 +363,9 @@ pcot_status pcot_pick(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype
 /*
  * The picker's building block with an explicit model and candidate list:
  * builds the features of the ncand candidates, normalises them with
- * mean/std (HOST, 12 + 12 floats), runs the MLP forward and argmin kernels
- * with the DEVICE parameters `mlp_params`, returns the index in *best
- * (HOST).  `scratch` is device memory of at least ncand * (12 + 2) * 4 + 256
+ * mean/std (HOST, 12 + 12 floats), runs the MLP forward and argmin (of the
+ * predicted slowdown, output 1) kernels with the DEVICE parameters
+ * `mlp_params`, returns the index in *best (HOST).  `scratch` is device memory of at least ncand * (12 + 2) * 4 + 256
  * bytes.  Synchronous.
  */
 pcot_status pcot_pick_among(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,

@@ -919,7 +919,6 @@ pcot_status features_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_d
     PCOT_TRY(make_ctx(h, sizes, nullptr, dtype, nullptr, &L));
     for (int i = 0; i < 12; ++i) f[i] = 0.f;
     f[0] = (float)L.geo.dims;
-    f[1] = (float)h->radius;
     for (int a = 0; a < L.geo.dims; ++a) f[2 + a] = log2f_safe((double)L.geo.n[a]);
     f[5] = log2f_safe((double)std::max<int64_t>(T, 1));
     f[11] = (float)dtype;
@@ -933,6 +932,9 @@ pcot_status features_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_d
     TileGeo tg;
     if (!choose_tiles(L, p ? p->tile : nullptr, k, &tg)) return PCOT_ERR_UNSUPPORTED;
     for (int a = 0; a < L.geo.dims; ++a) f[6 + a] = log2f_safe((double)tg.ext[a]);
+    double tiles = 1.0;
+    for (int a = 0; a < L.geo.dims; ++a) tiles *= (double)tg.count[a];
+    f[1] = log2f_safe(tiles);  // tiles per time block: the parallelism a block offers
     f[9] = log2f_safe((double)k);
     if (schedule == PCOT_COT) {
         double vol = 1.0;
@@ -959,7 +961,8 @@ pcot_tile_params tparams(int t0, int t1, int t2, int k, int h0 = 0, int h1 = 0, 
 }
 
 // MLP forward over the normalised features of every candidate and argmin of
-// the predicted time (output 0); candidates without a kernel never win.
+// the predicted slowdown against the problem's fastest candidate (output 1);
+// candidates without a kernel never win.
 pcot_status pick_among(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, const float* mlp_params,
                        const float* feat_mean, const float* feat_std, int ncand, const pcot_schedule* schedules,
                        const pcot_tile_params* params, void* scratch, int* best, cudaStream_t s) {
@@ -983,8 +986,9 @@ pcot_status pick_among(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtyp
     PCOT_CUDA(mlp::forward(mlp_params, dx, ncand, dy, s));
     const float big = 1e30f;
     for (int i = 0; i < ncand; ++i)
-        if (!ok[i]) PCOT_CUDA(cudaMemcpyAsync(dy + (size_t)i * 2, &big, sizeof(float), cudaMemcpyHostToDevice, s));
-    PCOT_CUDA(mlp::argmin(dy, ncand, 2, 0, didx, s));
+        if (!ok[i])
+            PCOT_CUDA(cudaMemcpyAsync(dy + (size_t)i * 2 + 1, &big, sizeof(float), cudaMemcpyHostToDevice, s));
+    PCOT_CUDA(mlp::argmin(dy, ncand, 2, 1, didx, s));
     int idx = -1;
     PCOT_CUDA(cudaMemcpyAsync(&idx, didx, sizeof(int), cudaMemcpyDeviceToHost, s));
     PCOT_CUDA(cudaStreamSynchronize(s));

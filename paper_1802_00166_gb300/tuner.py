@@ -72,12 +72,14 @@ def default_candidate(dims, dtype):
 
 # --------------------------------------------------------------- problems --
 
-def problem_set(seed, n2d, n3d):
+def problem_set(seed, n2d, n3d, n2d_f64=0):
     """Seeded Heat-2D (zero Dirichlet ring, sides log-uniform in [1024, 8192],
     T uniform in [64, 512]) and periodic Jacobi-3D (sides log-uniform in
-    [128, 512], T uniform in [16, 128]) problems, FP32."""
+    [128, 512], T uniform in [16, 128]) problems in FP32, and optionally
+    Heat-2D problems in FP64 exact mode (sides log-uniform in [512, 2048],
+    T uniform in [16, 128]; the FP64 pipe makes them slow to tune)."""
     import seeded_inputs as si
-    u = si.uniform01(seed, 2 * (n2d + n3d))
+    u = si.uniform01(seed, 2 * (n2d + n3d + n2d_f64))
     probs = []
     for i in range(n2d):
         side = int(round(1024 * 8 ** u[2 * i]))
@@ -89,6 +91,11 @@ def problem_set(seed, n2d, n3d):
         side -= side % 8
         T = 16 + min(int(u[2 * i + 1] * 113), 112)
         probs.append(dict(dims=3, sizes=(side, side, side), T=T, periodic=True))
+    for j in range(n2d_f64):
+        i = n2d + n3d + j
+        side = int(round(512 * 4 ** u[2 * i]))
+        T = 16 + min(int(u[2 * i + 1] * 113), 112)
+        probs.append(dict(dims=2, sizes=(side, side), T=T, periodic=False, dtype=pcot.PCOT_F64_EXACT))
     return probs
 
 
@@ -191,15 +198,28 @@ def tune_batched(h, grids, sizes, strides, Ts, dtype, stream, cands=None, reps=2
     return min(results, key=lambda r: r[1])[0], results
 
 
+# Largest slowdown the second target distinguishes: candidates more than 3x
+# slower than a problem's fastest are all "far off", and the loss spends its
+# capacity on ranking the candidates that compete for the pick.
+SLOWDOWN_CAP = math.log(3.0)
+
+
 def records_for(prob, cands, ms, feats, dtype=pcot.PCOT_F32):
+    """Training rows of one tuned problem: the candidate's features and two
+    measured targets, log milliseconds and the log slowdown against the
+    problem's fastest candidate (capped).  The picker chooses by the second:
+    it carries no per-problem scale, so the network's error goes into the
+    order of a problem's candidates, which is what a pick needs."""
     rows_x, rows_y = [], []
+    valid = [t for t in ms if t > 0]
+    if not valid:
+        return rows_x, rows_y
+    best = min(valid)
     for (sched, p), t, f in zip(cands, ms, feats):
         if t <= 0:
             continue
-        k = p.get("time_depth", 1) if sched != pcot.PCOT_SWEEP else 1
-        b = modelled_bytes(prob["sizes"], prob["T"], sched, k)
         rows_x.append(f)
-        rows_y.append([math.log(t), math.log(b)])
+        rows_y.append([math.log(t), min(math.log(t / best), SLOWDOWN_CAP)])
     return rows_x, rows_y
 
 
@@ -303,17 +323,18 @@ def evaluate(picker, probs, dtype=pcot.PCOT_F32, reps=2):
     rows = []
     rng = np.random.default_rng(5)
     for prob in probs:
-        cands, ms, feats = tune_problem(prob, dtype, reps)
+        dt = prob.get("dtype", dtype)
+        cands, ms, feats = tune_problem(prob, dt, reps)
         valid = [i for i, t in enumerate(ms) if t > 0]
         best = min(ms[i] for i in valid)
         coeffs = {2: HEAT2D, 3: JAC3D}[prob["dims"]]
         h = pcot.pcot_create(prob["dims"], 1, coeffs,
                              pcot.PCOT_PERIODIC if prob["periodic"] else pcot.PCOT_DIRICHLET)
         try:
-            i_pick = picker.pick(h, prob["sizes"], prob["T"], dtype, cands)
+            i_pick = picker.pick(h, prob["sizes"], prob["T"], dt, cands)
         finally:
             pcot.pcot_destroy(h)
-        dflt = default_candidate(prob["dims"], dtype)
+        dflt = default_candidate(prob["dims"], dt)
         i_def = next((i for i, c in enumerate(cands) if c[0] == dflt[0] and c[1] == dflt[1]), valid[0])
         i_rand = int(rng.choice(valid))
         rows.append(dict(prob=prob, best_ms=best, pick_ms=ms[i_pick], default_ms=ms[i_def], random_ms=ms[i_rand],
@@ -338,16 +359,18 @@ def main():
     t.add_argument("--problems3d", type=int, default=120)
     t.add_argument("--heldout2d", type=int, default=32)
     t.add_argument("--heldout3d", type=int, default=32)
-    t.add_argument("--steps", type=int, default=6000)
+    t.add_argument("--problems2d-f64", type=int, default=40)
+    t.add_argument("--steps", type=int, default=10000)
     args = ap.parse_args()
     from paper_1802_00166_gb300 import build
     build.build()
     os.makedirs(args.out, exist_ok=True)
     t0 = time.time()
     X, Y, meta = [], [], []
-    for pi, prob in enumerate(problem_set(4, args.problems2d, args.problems3d)):
-        cands, ms, feats = tune_problem(prob)
-        rx, ry = records_for(prob, cands, ms, feats)
+    for pi, prob in enumerate(problem_set(4, args.problems2d, args.problems3d, args.problems2d_f64)):
+        dt = prob.get("dtype", pcot.PCOT_F32)
+        cands, ms, feats = tune_problem(prob, dt)
+        rx, ry = records_for(prob, cands, ms, feats, dt)
         X += rx
         Y += ry
         meta.append(dict(prob=prob, best_ms=min(v for v in ms if v > 0)))
@@ -358,7 +381,7 @@ def main():
     picker, hist = train(X, Y, steps=args.steps)
     picker.save(os.path.join(args.out, "picker.npz"))
     held = problem_set(5, args.heldout2d, args.heldout3d)
-    summary, rows = evaluate(picker, held)
+    summary, rows = evaluate(picker, held, reps=3)
     report = dict(records=int(X.shape[0]), problems=len(meta), collect_seconds=t_collect, loss_history=hist,
                   heldout=summary, rows=[dict(sizes=r["prob"]["sizes"], T=r["prob"]["T"], best_ms=r["best_ms"],
                                               pick_ms=r["pick_ms"], default_ms=r["default_ms"],

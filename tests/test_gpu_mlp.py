@@ -105,7 +105,7 @@ def test_autotune_and_pick_consistency():
     i = picker.pick(h, prob["sizes"], prob["T"], pcot.PCOT_F32, cands)
     pcot.pcot_destroy(h)
     pred = picker.predict((feats - picker.feat_mean) / picker.feat_std)
-    assert i == int(np.argmin(pred[:, 0]))
+    assert i == int(np.argmin(pred[:, 1]))   # picks minimise the predicted slowdown
 
 
 @pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -113,11 +113,13 @@ def test_autotune_and_pick_consistency():
                     reason="no trained picker weights committed")
 def test_trained_picker_regret_on_heldout_sample():
     """The committed model picks within 10% (time-weighted) of the exhaustive
-    tuner's best on a held-out sample, and beats the fixed default tile."""
+    tuner's best on a held-out sample re-timed now, no pick is more than 30%
+    off (timing noise included), and it beats the fixed default tile."""
     from paper_1802_00166_gb300 import tuner
     picker = tuner.Picker.load()
     held = tuner.problem_set(5, 32, 32)
     sample = held[0:32:8] + held[32:64:8]
     summary, rows = tuner.evaluate(picker, sample)
     assert summary["regret_time_weighted"] <= 0.10, summary
+    assert summary["regret_max"] <= 0.30, summary
     assert summary["regret_mean"] <= summary["default_regret_mean"], summary

@@ -334,3 +334,27 @@ def test_strided_padding_untouched(dims, sched, T):
     torch.as_strided(mask, shape, st, 512).fill_(False)
     assert np.all(base[mask].cpu().numpy() == -777.0)
     pcot.pcot_destroy(h)
+
+
+@pytest.mark.parametrize("k", [4, 6, 8])
+@pytest.mark.parametrize("sizes", [(33, 130), (190, 517), (257, 1000)])
+def test_heat2d_f32_recursive_single_span_tiles(k, sizes):
+    """Recursive order with one-span tiles on rows padded to 128 bytes (the
+    persistent kernel whose stages are split over several warps): bitwise
+    equal to the sweep (every FMA-mode kernel rounds the same way), within the
+    FP32 tolerance of the oracle, with asymmetric coefficients and a random
+    ring so that the Dirichlet pass-through and every operand's orientation
+    are exercised."""
+    c = si.random_coefficients(2, 1, 70 + k) * 0.2 + np.array([0.2, 0.2, 0.2, 0.2, 0.2])
+    h = _handle(2, coeffs=c)
+    g32 = si.uniform_grid(sizes, 23 + k, ring="random", dtype=np.float32)
+    T = 2 * k + 7
+    st = padded_strides(g32.shape, 4, 128)
+    ref = run_gpu(h, g32, sizes, T, pcot.PCOT_F32, pcot.PCOT_SWEEP, strides=st)
+    for H in (16, 24, 80):
+        p = pcot.tile_params(tile=(H, 112), time_depth=k, cot_threshold=(2, 3, 2))
+        got = run_gpu(h, g32, sizes, T, pcot.PCOT_F32, pcot.PCOT_COT, p, strides=st)
+        assert np.array_equal(got, ref), (k, sizes, H)
+    assert oracle.max_rel_error(oracle.interior(got, sizes), oracle.interior(oracle.sweep(g32, sizes, c, T), sizes)) \
+        <= 1e-5
+    pcot.pcot_destroy(h)
