@@ -451,7 +451,9 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         j1, j1_out = run_jacobi1d(pcot, stream, args.steps)
         j3, j3_out = run_jacobi3d(pcot, stream, args.steps, peak)
-        configs = {"jacobi1d": j1, "jacobi3d": j3, "batched": run_batched(pcot, stream, args.steps)}
+        f64, f64_out = run_heat2d_f64(pcot, stream, args.steps, g0)
+        configs = {"jacobi1d": j1, "jacobi3d": j3, "batched": run_batched(pcot, stream, args.steps),
+                   "heat2d_f64": f64}
     if rank == 0 and not args.no_cpu_baseline:
         cpu, ref = _cpu_oracle_heat2d(g0, full=extra)
         line["cpu_baseline"] = cpu
@@ -462,6 +464,11 @@ def run_gpu(args):
                                  bound=1e-5)
         if extra:
             _cpu_leg_configs(configs, j1_out, j3_out)
+            if ref is not None:
+                import numpy as np
+                configs["heat2d_f64"]["bitwise_equal_to_oracle"] = {
+                    k: bool(np.array_equal(v, ref)) for k, v in f64_out.items()}
+            del f64_out
     if configs:
         line["configs"] = configs
     if (args.gs2d or args.fdtd2d or args.la) and rank == 0:
@@ -580,6 +587,65 @@ def run_jacobi3d(pcot, stream, steps, peak):
     del dev
     torch.cuda.empty_cache()
     return out, (g32, result)
+
+
+# Heat-2D 8192^2 FP64 exact mode (bitwise the loop nest), T = 512: the sweep,
+# the best overlapped tiles (single-level, depth 1) and the non-redundant
+# parallelogram tiles of the skewed space.  The DP pipe bounds all three.
+F64_RUNS = [("sweep", "sweep", None), ("slt_k1", "slt", dict(tile=(64, 0), time_depth=1)),
+            ("skew", "skew", dict(tile=(32, 64), time_depth=4))]
+F64_HEAD = "skew"
+# Nominal FP64 rate of GB300, 1.25 TFLOP/s, counting an FMA as two flops:
+# 152 SMs x 2 DP instructions per clock x 2.07 GHz.  FP64 exact mode issues
+# 9 DP instructions per update (5 multiplies, 4 adds).
+DP_INSTR_PER_S = 152 * 2 * 2.07e9
+F64_EXACT_INSTR_PER_UPDATE = 9
+
+
+def run_heat2d_f64(pcot, stream, steps, g0):
+    """Heat-2D on the benchmark's grid (its FP32 seeded values widened) in
+    FP64 exact mode on the schedules of F64_RUNS, each with its fraction of
+    the DP-pipe roof; results kept for the bitwise check against the oracle's
+    512 steps on the same widened inputs (computed in the CPU leg)."""
+    import numpy as np
+    import torch
+    n, T = N_SIDE, T_STEPS
+    sizes = (n, n)
+    h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
+    pitch = ((n + 2) * 8 + 127) // 128 * 128 // 8
+    strides = (pitch, 1)
+    base = torch.zeros((n + 2) * pitch, dtype=torch.float64, device="cuda")
+    view = torch.as_strided(base, (n + 2, n + 2), strides)
+    src = torch.from_numpy(g0.astype(np.float64)).cuda()
+    roof_gu = DP_INSTR_PER_S / F64_EXACT_INSTR_PER_UPDATE / 1e9
+    out = {"workload": f"heat2d-5pt {n}^2 T={T} fp64-exact Dirichlet (the benchmark's grid, widened)",
+           "head": F64_HEAD, "bound": "alu",
+           "peak": {"GUpdates/s": roof_gu, "basis": "nominal 1.25 TFLOP/s FP64 = 152 SMs x 2 DP instr/clk x 2.07 GHz, "
+                                                  "9 DP instructions per update"}}
+    results = {}
+    for name, sname, prm in F64_RUNS:
+        sched = pcot.SCHEDULES[sname]
+        p = pcot.tile_params(**prm) if prm else None
+        nb = pcot.pcot_workspace_bytes(h, sizes, strides, T, pcot.PCOT_F64_EXACT, sched, p)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        run = lambda: pcot.pcot_run(h, view.data_ptr(), ws.data_ptr(), nb, sizes, strides, T,
+                                    pcot.PCOT_F64_EXACT, sched, p, stream)
+        ms = _time_runs(run, max(3, min(steps, 5)), stream)
+        gu = n * n * T / ms / 1e6
+        out[name] = {"ms": ms, "GUpdates/s": gu, "alu_frac": gu / roof_gu, "params": prm}
+        view.copy_(src)
+        run()
+        torch.cuda.synchronize()
+        st = pcot.pcot_check(h, stream)
+        if st != pcot.PCOT_OK:
+            raise pcot.PcotError(st, "heat2d fp64 " + name)
+        results[name] = view.cpu().numpy()
+        del ws
+    out["speedup_vs_sweep"] = out["sweep"]["ms"] / out[F64_HEAD]["ms"]
+    pcot.pcot_destroy(h)
+    del base, view, src
+    torch.cuda.empty_cache()
+    return out, results
 
 
 def _cpu_oracle_heat2d(g0, full=True, seconds=12.0):
@@ -994,18 +1060,20 @@ def run_profile_case(args):
         return 0
     H, W = (int(v) for v in args.case_tile.split(","))
     h = pcot.pcot_create(2, 1, HEAT2D, pcot.PCOT_DIRICHLET)
-    pitch = ((n + 2 + 31) // 32) * 32
-    base = torch.rand((n + 2) * pitch, device="cuda")
+    dt = pcot.DTYPES[args.case_dtype]
+    elem = 4 if dt == pcot.PCOT_F32 else 8
+    pitch = ((n + 2) * elem + 127) // 128 * 128 // elem          # rows padded to 128 bytes
+    base = torch.rand((n + 2) * pitch, device="cuda", dtype=torch.float32 if elem == 4 else torch.float64)
     p = pcot.tile_params(tile=(H, W), time_depth=args.case_k, cot_threshold=th)
-    nb = pcot.pcot_workspace_bytes(h, (n, n), (pitch, 1), T, pcot.PCOT_F32, sched, p)
+    nb = pcot.pcot_workspace_bytes(h, (n, n), (pitch, 1), T, dt, sched, p)
     ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
     for _ in range(args.case_runs):
-        pcot.pcot_run(h, base.data_ptr(), ws.data_ptr(), nb, (n, n), (pitch, 1), T, pcot.PCOT_F32, sched, p)
+        pcot.pcot_run(h, base.data_ptr(), ws.data_ptr(), nb, (n, n), (pitch, 1), T, dt, sched, p)
     st = pcot.pcot_check(h)
     pcot.pcot_destroy(h)
     if st != pcot.PCOT_OK:
         raise pcot.PcotError(st, "profile case")
-    print(f"ok {args.profile_case} n={n} T={T} k={args.case_k} tile={H},{W} theta={th}")
+    print(f"ok {args.profile_case} {args.case_dtype} n={n} T={T} k={args.case_k} tile={H},{W} theta={th}")
     return 0
 
 
@@ -1022,7 +1090,7 @@ def main():
     ap.add_argument("--gs2d", action="store_true", help="also time Gauss-Seidel 2-D at the paper's size")
     ap.add_argument("--fdtd2d", action="store_true", help="also time FDTD-2D at the paper's size")
     ap.add_argument("--la", action="store_true", help="also time LU and Cholesky at the paper's sizes")
-    ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot"],
+    ap.add_argument("--profile-case", default=None, choices=[None, "sweep", "slt", "cot", "skew"],
                     help="run one Heat-2D configuration (no timing) for a profiler")
     ap.add_argument("--case-dims", type=int, default=2, choices=[2, 3])
     ap.add_argument("--case-la", default=None, choices=[None, "lu", "cholesky"],
@@ -1033,6 +1101,8 @@ def main():
     ap.add_argument("--case-tile", default="96,112")
     ap.add_argument("--case-theta", default="2,256,256")
     ap.add_argument("--case-runs", type=int, default=2)
+    ap.add_argument("--case-dtype", default="f32", choices=["f32", "f64", "f64_exact"],
+                    help="profile case: arithmetic of a 2-D stencil case")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)

@@ -21,6 +21,15 @@
  *               the lattice of (time block, spatial tile) leaves after time
  *               skewing, run by one persistent kernel with dependency counters
  *               in place of the OpenMP task waits of Sec. 4.2.
+ *   PCOT_SKEW   (2-D Dirichlet grids) parallelogram tiles of the skewed space
+ *               (t, t+i, t+j) -- the tiles of Sec. 3.1 after the skew of Sec.
+ *               4.3.2, which recompute nothing -- run by the same persistent
+ *               executor in wavefront order, or in the recursive order of Sec.
+ *               4 when cot_threshold is set.  tile[0], tile[1] are the tile's
+ *               skewed extents (default 32, 64), time_depth its steps
+ *               (default 4), tile[2] the threads per CTA (32..512, a multiple
+ *               of 32; default 256).  Every point is computed once, in the
+ *               loop nest's rounding: FP64 exact mode is bitwise the sweep.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -79,7 +88,7 @@ typedef enum {
 
 typedef enum { PCOT_DIRICHLET = 0, PCOT_PERIODIC = 1 } pcot_boundary;
 typedef enum { PCOT_F32 = 0, PCOT_F64 = 1, PCOT_F64_EXACT = 2 } pcot_dtype;
-typedef enum { PCOT_SWEEP = 0, PCOT_SLT = 1, PCOT_COT = 2, PCOT_AUTO = 3 } pcot_schedule;
+typedef enum { PCOT_SWEEP = 0, PCOT_SLT = 1, PCOT_COT = 2, PCOT_AUTO = 3, PCOT_SKEW = 4 } pcot_schedule;
 
 /*
  * Tile parameters (Sec. 3.3 "Tile Size": the tile size doubles as the
@@ -188,6 +197,18 @@ pcot_status pcot_plan_query(pcot_handle h, const int64_t *sizes, int64_t T, pcot
                             const pcot_tile_params *params, int32_t *lattice, int32_t *tile_ext,
                             int32_t *depth, int64_t *n_tiles, int64_t *tail_steps,
                             int32_t *queue, int32_t *deps, int64_t cap);
+
+/*
+ * Describe the PCOT_SKEW plan of a 2-D problem (no GPU needed; for the
+ * planner tests).  lattice[3] = tiles along t, a = t+i, c = t+j; tile[3] =
+ * (time_depth, tile[0], tile[1]) used; *n_tiles = non-empty tiles.  If
+ * `queue` is non-NULL it receives the n_tiles lattice ids (b0 * L1 + b1) * L2
+ * + b2 in execution order and `deps` (may be NULL) each one's number of
+ * non-empty predecessors among its seven lower neighbours (capacity `cap`).
+ */
+pcot_status pcot_skew_plan_query(const int64_t *sizes, int64_t T, const pcot_tile_params *params,
+                                 int32_t *lattice, int32_t *tile, int64_t *n_tiles, int32_t *queue,
+                                 int32_t *deps, int64_t cap);
 
 /*
  * Test hook: the persistent executor's dependency wait with a counter that

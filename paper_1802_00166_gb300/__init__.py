@@ -36,8 +36,9 @@ PCOT_SWEEP = 0
 PCOT_SLT = 1
 PCOT_COT = 2
 PCOT_AUTO = 3
+PCOT_SKEW = 4
 
-SCHEDULES = {"sweep": PCOT_SWEEP, "slt": PCOT_SLT, "cot": PCOT_COT, "auto": PCOT_AUTO}
+SCHEDULES = {"sweep": PCOT_SWEEP, "slt": PCOT_SLT, "cot": PCOT_COT, "auto": PCOT_AUTO, "skew": PCOT_SKEW}
 
 PCOT_LA_LU = 0
 PCOT_LA_CHOLESKY = 1
@@ -126,6 +127,8 @@ def _load():
                               ctypes.c_int, ctypes.POINTER(pcot_tile_params), _VP]),
         "pcot_gs2d_plan_query": (S, [_I64P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(pcot_tile_params), _I32P,
                                      _I32P, _I64P, _I32P, _I32P, ctypes.c_int64]),
+        "pcot_skew_plan_query": (S, [_I64P, ctypes.c_int64, ctypes.POINTER(pcot_tile_params), _I32P, _I32P, _I64P,
+                                     _I32P, _I32P, ctypes.c_int64]),
         "pcot_fdtd2d_workspace_bytes": (S, [_I64P, _I64P, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(pcot_tile_params), ctypes.POINTER(ctypes.c_size_t)]),
         "pcot_fdtd2d_run": (S, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _I64P, _I64P, ctypes.c_int64,
@@ -156,7 +159,7 @@ def _load():
 
 def exported_symbols():
     """Names declared in include/pcot.h that this binding marshals."""
-    return ["pcot_gs2d_workspace_bytes", "pcot_gs2d_run", "pcot_gs2d_plan_query",
+    return ["pcot_gs2d_workspace_bytes", "pcot_gs2d_run", "pcot_gs2d_plan_query", "pcot_skew_plan_query",
             "pcot_fdtd2d_workspace_bytes", "pcot_fdtd2d_run",
             "pcot_la_workspace_bytes", "pcot_la_run", "pcot_la_plan_query",
             "pcot_status_string", "pcot_create", "pcot_destroy", "pcot_workspace_bytes", "pcot_run",
@@ -300,6 +303,25 @@ def pcot_gs2d_plan_query(sizes, T, schedule, params=None, with_queue=True):
         out["queue"] = qq[:nt.value].copy()
         out["deps"] = dd[:ncell].copy()
     return out
+
+
+def pcot_skew_plan_query(sizes, T, params=None):
+    """PCOT_SKEW plan of a 2-D problem: lattice, tile, n_tiles, and the queue
+    of lattice ids in execution order with each entry's predecessor count."""
+    lib = _load()
+    s = _i64(sizes)
+    lat = (ctypes.c_int32 * 3)()
+    tl = (ctypes.c_int32 * 3)()
+    nt = ctypes.c_int64()
+    _chk(lib.pcot_skew_plan_query(_p64(s), int(T), _params(params), lat, tl, ctypes.byref(nt), None, None, 0),
+         "pcot_skew_plan_query")
+    cap = max(nt.value, 1)
+    qq = np.zeros(cap, dtype=np.int32)
+    dd = np.zeros(cap, dtype=np.int32)
+    _chk(lib.pcot_skew_plan_query(_p64(s), int(T), _params(params), None, None, None, qq.ctypes.data_as(_I32P),
+                                  dd.ctypes.data_as(_I32P), cap), "pcot_skew_plan_query")
+    return dict(lattice=list(lat), tile=list(tl), n_tiles=nt.value, queue=qq[:nt.value].copy(),
+                deps=dd[:nt.value].copy())
 
 
 def pcot_fdtd2d_workspace_bytes(sizes, strides, T, dtype, schedule, params=None):

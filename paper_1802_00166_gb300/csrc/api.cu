@@ -72,6 +72,7 @@ struct pcot_plan {
     double* d_partials = nullptr;  // grid-sum partials
     std::map<std::string, CotPlanHost*> cot_cache;
     std::map<std::string, GsPlanCache*> gs_cache;
+    std::map<std::string, GsPlanCache*> skew_cache;
     std::map<std::string, FdPlanCache*> fd_cache;
     std::map<std::string, LaPlanCache*> la_cache;
     uint64_t timeout_ns = kDefaultTimeoutNs;
@@ -282,6 +283,129 @@ pcot_status run_blocks(pcot_handle h, const LaunchCtx& L, const pcot_tile_params
 }
 
 // The candidates the picker chooses among and its choice for a problem
+// ---- PCOT_SKEW: parallelogram tiles of the skewed space (t, t+i, t+j) ----
+
+// Tile shape {time steps, skewed rows, skewed columns}, threads per CTA and
+// order of a PCOT_SKEW run: the recursive order when cot_threshold[0] is set
+// (missing entries 32), else the wavefront order.
+bool skew_shape(const pcot_tile_params* p, int32_t* tile, int* recursive, int32_t* theta, int* threads = nullptr) {
+    tile[0] = (p && p->time_depth > 0) ? p->time_depth : 4;
+    tile[1] = (p && p->tile[0] > 0) ? p->tile[0] : 32;
+    tile[2] = (p && p->tile[1] > 0) ? p->tile[1] : 64;
+    const int thr = (p && p->tile[2] > 0) ? p->tile[2] : 256;
+    if (threads) *threads = thr;
+    *recursive = (p && p->cot_threshold[0] > 0) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) theta[d] = (p && p->cot_threshold[d] > 0) ? p->cot_threshold[d] : 32;
+    return tile[0] <= 256 && tile[1] >= 2 && tile[1] <= 1024 && tile[2] >= 2 && tile[2] <= 1024 && thr >= 32 &&
+           thr <= 512 && thr % 32 == 0;
+}
+
+// Upload-image bytes that suffice for any plan of this shape: head block,
+// the counter of every lattice id, and a queue of at most every id.
+pcot_status skew_image_bound(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, size_t* bytes) {
+    const int64_t ext[3] = {T, T - 1 + n0, T - 1 + n1};
+    int64_t cells = 1;
+    for (int d = 0; d < 3; ++d) {
+        cells *= (ext[d] + tile[d] - 1) / tile[d];
+        if (cells > (int64_t)1 << 28) return PCOT_ERR_UNSUPPORTED;
+    }
+    *bytes = kAlign + round_up((size_t)cells * 4, kAlign) + round_up((size_t)cells * 4 + 4, kAlign);
+    return PCOT_OK;
+}
+
+pcot_status skew_get_plan(pcot_handle h, int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive,
+                          const int32_t* theta, GsPlanCache** out) {
+    char key[160];
+    snprintf(key, sizeof(key), "%lld,%lld,%lld,%d,%d,%d,%d,%d,%d,%d", (long long)n0, (long long)n1, (long long)T,
+             recursive, tile[0], tile[1], tile[2], theta[0], theta[1], theta[2]);
+    if (h) {
+        auto it = h->skew_cache.find(key);
+        if (it != h->skew_cache.end()) {
+            *out = it->second;
+            return PCOT_OK;
+        }
+    }
+    GsPlanCache* c = new GsPlanCache();
+    if (!skew_plan(n0, n1, T, tile, recursive, theta, &c->plan)) {
+        delete c;
+        return PCOT_ERR_UNSUPPORTED;
+    }
+    for (int d = 0; d < 3; ++d) c->tile[d] = tile[d];
+    c->counts_bytes = round_up(c->plan.deps.size() * 4, kAlign);
+    c->image_bytes = kAlign + c->counts_bytes + round_up(c->plan.queue.size() * 4 + 4, kAlign);
+    if (h) {
+        if (h->skew_cache.size() >= 16) {
+            for (auto& kv : h->skew_cache) {
+                if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+                delete kv.second;
+            }
+            h->skew_cache.clear();
+        }
+        h->skew_cache[key] = c;
+    }
+    *out = c;
+    return PCOT_OK;
+}
+
+// Even time levels live in the grid, odd ones in the twin; one persistent
+// launch runs every tile, and an odd T ends with a copy of the twin back.
+pcot_status run_skew(pcot_handle h, const LaunchCtx& L, void* grid, void* workspace, size_t ws_bytes, int64_t T,
+                     const pcot_tile_params* params) {
+    if (L.geo.dims != 2 || L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
+    int32_t tl[3], th[3];
+    int rec = 0, threads = 0;
+    if (!skew_shape(params, tl, &rec, th, &threads)) return PCOT_ERR_INVALID_ARG;
+    const int64_t n0 = L.geo.n[0], n1 = L.geo.n[1];
+    size_t extra = 0;
+    PCOT_TRY(skew_image_bound(n0, n1, T, tl, &extra));
+    if (ws_bytes < twin_bytes(L) + extra) return PCOT_ERR_OOM;
+    SkewDev q;
+    std::memset(&q, 0, sizeof(q));
+    for (int d = 0; d < 3; ++d) q.tile[d] = tl[d];
+    skew2d_window(&q);
+    if (skew2d_smem_bytes(L.dtype, q) > 227 * 1024) return PCOT_ERR_UNSUPPORTED;
+    PCOT_TRY(ensure_device(h));
+    GsPlanCache* c = nullptr;
+    PCOT_TRY(skew_get_plan(h, n0, n1, T, tl, rec, th, &c));
+    if (!c->pinned) {
+        void* p = nullptr;
+        PCOT_CUDA(cudaMallocHost(&p, c->image_bytes));
+        unsigned char* img = (unsigned char*)p;
+        std::memset(img, 0, c->image_bytes);
+        std::memcpy(img + kAlign, c->plan.deps.data(), c->plan.deps.size() * 4);
+        std::memcpy(img + kAlign + c->counts_bytes, c->plan.queue.data(), c->plan.queue.size() * 4);
+        c->pinned = p;
+    }
+    void* twin = workspace;
+    PCOT_CUDA(launch_ring_copy(L, grid, twin));
+    ++h->launches;
+    if (c->plan.queue.empty()) return PCOT_OK;
+    unsigned char* ws = (unsigned char*)workspace + twin_bytes(L);
+    PCOT_CUDA(cudaMemcpyAsync(ws, c->pinned, c->image_bytes, cudaMemcpyHostToDevice, L.stream));
+    q.head = (int32_t*)ws;
+    q.counts = (int32_t*)(ws + kAlign);
+    q.queue = (const int32_t*)(ws + kAlign + c->counts_bytes);
+    q.ntiles = (int64_t)c->plan.queue.size();
+    for (int d = 0; d < 3; ++d) q.lattice[d] = c->plan.lattice[d];
+    q.n0 = n0;
+    q.n1 = n1;
+    q.T = T;
+    q.pitch = L.geo.s[0];
+    q.status = h->d_status;
+    q.timeout_ns = h->timeout_ns;
+    const int per_sm = skew2d_ctas_per_sm(L.dtype, q, threads);
+    if (per_sm < 1) return PCOT_ERR_UNSUPPORTED;
+    int64_t nctas = (int64_t)per_sm * h->num_sms;
+    if (nctas > q.ntiles) nctas = q.ntiles;
+    PCOT_CUDA(launch_skew2d(L, grid, twin, q, (int)nctas, threads));
+    ++h->launches;
+    if (T & 1) {
+        PCOT_CUDA(launch_grid_copy(L, twin, grid));
+        ++h->launches;
+    }
+    return PCOT_OK;
+}
+
 // (PCOT_AUTO, pcot_pick); defined with the picker below.
 std::vector<std::pair<pcot_schedule, pcot_tile_params>> pick_candidates(int dims, pcot_dtype dtype, bool periodic);
 pcot_status pick_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, cudaStream_t s,
@@ -296,13 +420,15 @@ pcot_status run_impl(pcot_handle h, void* grid, void* workspace, size_t ws_bytes
     PCOT_TRY(make_ctx(h, sizes, strides, dtype, stream, &L));
     if (((uintptr_t)grid % elem_size(dtype)) != 0) return PCOT_ERR_ALIGNMENT;
     if (((uintptr_t)workspace % kAlign) != 0) return PCOT_ERR_ALIGNMENT;
-    if (schedule < PCOT_SWEEP || schedule > PCOT_AUTO) return PCOT_ERR_INVALID_ARG;
+    if (schedule < PCOT_SWEEP || schedule > PCOT_SKEW) return PCOT_ERR_INVALID_ARG;
+    if (schedule == PCOT_SKEW && (L.geo.dims != 2 || L.geo.periodic)) return PCOT_ERR_UNSUPPORTED;
     if (T == 0) return PCOT_OK;
     pcot_tile_params picked;
     if (schedule == PCOT_AUTO) {
         PCOT_TRY(pick_impl(h, sizes, T, dtype, (cudaStream_t)stream, &schedule, &picked));
         params = &picked;
     }
+    if (schedule == PCOT_SKEW) return run_skew(h, L, grid, workspace, ws_bytes, T, params);
     if (schedule == PCOT_COT && L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
     if (ws_bytes < twin_bytes(L)) return PCOT_ERR_OOM;
     CotPlanHost* cplan = nullptr;
@@ -423,6 +549,10 @@ pcot_status pcot_destroy(pcot_handle h) {
         if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
         delete kv.second;
     }
+    for (auto& kv : h->skew_cache) {
+        if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+        delete kv.second;
+    }
     for (auto& kv : h->fd_cache) {
         if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
         delete kv.second;
@@ -452,6 +582,17 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t* sizes, const int6
             size_t bc = 0;
             if (pcot_workspace_bytes(h, sizes, strides, T, dtype, c.first, &c.second, &bc) == PCOT_OK)
                 b = std::max(b, bc);
+        }
+    }
+    if (schedule == PCOT_SKEW) {
+        if (L.geo.dims != 2 || L.geo.periodic) return PCOT_ERR_UNSUPPORTED;
+        int32_t tl[3], th[3];
+        int rec = 0;
+        if (!skew_shape(params, tl, &rec, th)) return PCOT_ERR_INVALID_ARG;
+        if (T > 0) {
+            size_t extra = 0;
+            PCOT_TRY(skew_image_bound(L.geo.n[0], L.geo.n[1], T, tl, &extra));
+            b += extra;
         }
     }
     if (schedule == PCOT_COT && T > 0) {
@@ -1340,6 +1481,31 @@ pcot_status pcot_gs2d_plan_query(const int64_t* sizes, int64_t T, pcot_schedule 
         for (int64_t k = 0; k < cap && k < (int64_t)c->plan.queue.size(); ++k) queue[k] = c->plan.queue[(size_t)k];
     if (deps)
         for (int64_t k = 0; k < cap && k < (int64_t)c->plan.deps.size(); ++k) deps[k] = c->plan.deps[(size_t)k];
+    delete c;
+    return PCOT_OK;
+}
+
+pcot_status pcot_skew_plan_query(const int64_t* sizes, int64_t T, const pcot_tile_params* params,
+                                 int32_t* lattice, int32_t* tile, int64_t* n_tiles, int32_t* queue, int32_t* deps,
+                                 int64_t cap) {
+    int64_t pitch = 0;
+    PCOT_TRY(gs_check_args(sizes, nullptr, T, &pitch));
+    if (T < 1) return PCOT_ERR_INVALID_ARG;
+    int32_t tl[3], th[3];
+    int rec = 0;
+    if (!skew_shape(params, tl, &rec, th)) return PCOT_ERR_INVALID_ARG;
+    GsPlanCache* c = nullptr;
+    PCOT_TRY(skew_get_plan(nullptr, sizes[0], sizes[1], T, tl, rec, th, &c));
+    for (int d = 0; d < 3; ++d) {
+        if (lattice) lattice[d] = c->plan.lattice[d];
+        if (tile) tile[d] = tl[d];
+    }
+    if (n_tiles) *n_tiles = (int64_t)c->plan.queue.size();
+    if (queue)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.queue.size(); ++k) queue[k] = c->plan.queue[(size_t)k];
+    if (deps)
+        for (int64_t k = 0; k < cap && k < (int64_t)c->plan.queue.size(); ++k)
+            deps[k] = c->plan.deps[(size_t)c->plan.queue[(size_t)k]];
     delete c;
     return PCOT_OK;
 }

@@ -62,6 +62,27 @@ size_t gs2d_smem_bytes(int dtype, const GsDev& q);
 int gs2d_ctas_per_sm(int dtype, const GsDev& q);
 cudaError_t launch_gs2d(int dtype, void* grid, const GsDev& q, int nctas, cudaStream_t s);
 
+// ---- k_skew2d.cu: 2-D Jacobi star stencil on parallelogram tiles of the skewed (t, t+i, t+j) space ----
+struct SkewDev {
+    const int32_t* queue;  // non-empty tile ids in execution order
+    int32_t* counts;       // remaining predecessors per lattice id
+    int32_t* head;         // next queue position to pop
+    int64_t ntiles;
+    int32_t lattice[3];    // tiles along t, a = t+i, c = t+j
+    int32_t tile[3];       // kt, ha, wc (skewed points per tile)
+    int64_t n0, n1, T;     // interior rows, columns, time steps
+    int64_t pitch;         // row stride of both buffers (elements)
+    int32_t rows, cols;    // shared-memory window of a tile (halo included)
+    DevStatus* status;
+    uint64_t timeout_ns;
+};
+// Window geometry of a tile and its shared-memory bytes (a window of each buffer).
+void skew2d_window(SkewDev* q);
+size_t skew2d_smem_bytes(int dtype, const SkewDev& q);
+int skew2d_ctas_per_sm(int dtype, const SkewDev& q, int threads);
+// buf0 holds the even time levels, buf1 the odd ones.
+cudaError_t launch_skew2d(const LaunchCtx& L, void* buf0, void* buf1, const SkewDev& q, int nctas, int threads);
+
 // ---- k_fdtd2d.cu: FDTD-2D (three fields, two copies) ----
 struct FdDev {
     int64_t nx, ny;        // field rows and columns

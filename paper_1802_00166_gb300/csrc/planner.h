@@ -51,6 +51,15 @@ struct GsPlanHost {
 bool gs_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
              GsPlanHost* out);
 
+// Skewed-tile plan of a 2-D Jacobi star stencil (planner_gs.cpp, same orders
+// and dependency rule): tiles of the skewed space (t, a, c) = (t, t + i,
+// t + j), 0 <= t < T, 1 <= i <= n0, 1 <= j <= n1; tile = {kt, ha, wc} with
+// ha, wc >= 2.  Every flow and two-buffer anti dependence has components in
+// {0, 1, 2}, so the tiles are parallelograms that recompute nothing and
+// depend only on their seven lower lattice neighbours.
+bool skew_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
+               GsPlanHost* out);
+
 // LU / Cholesky tile plan (planner_la.cpp): the non-empty tiles
 // (kb * L + ib) * L + jb of the b x b x b lattice over the (k, i, j) space in
 // execution order (lexicographic, or the recursive order when `recursive`),

@@ -1,5 +1,7 @@
-// Tile planner for Gauss-Seidel 2-D (GS-2D, Sec. 5.1.2): the in-place,
-// lexicographic 9-point average.
+// Tile planners over skewed 3-D lattices: Gauss-Seidel 2-D (GS-2D, Sec.
+// 5.1.2; the in-place, lexicographic 9-point average) and the two-buffer 2-D
+// Jacobi star stencil tiled by parallelograms of its skewed space (skew_plan
+// at the end; the same orders and dependency rule, another skew).
 //
 // The iteration space (t, i, j) is skewed to (t, a, c) = (t, t + i, 2t + i + j):
 // a point reads its north row and west neighbour at step t and its own, east
@@ -31,6 +33,8 @@ namespace pcot {
 
 namespace {
 
+// A 3-D lattice of tiles with a per-tile emptiness flag; the orders and
+// dependency counts below depend on nothing else.
 struct GsLattice {
     int64_t n0, n1, T;
     int32_t tile[3];
@@ -75,14 +79,16 @@ bool tile_nonempty(const GsLattice& g, int64_t b0, int64_t b1, int64_t b2) {
     return false;
 }
 
-void build_lattice(GsLattice& g) {
-    const int64_t ext[3] = {g.T, g.T - 1 + g.n0, 2 * g.T - 3 + g.n0 + g.n1};
+// Lattice extents, emptiness flags (by `nonempty(b0, b1, b2)`) and the prefix
+// counts used to test orthants for emptiness.
+template <class F>
+void build_lattice(GsLattice& g, const int64_t* ext, F nonempty) {
     for (int d = 0; d < 3; ++d) g.L[d] = (int32_t)((ext[d] + g.tile[d] - 1) / g.tile[d]);
     const int64_t n = (int64_t)g.L[0] * g.L[1] * g.L[2];
     g.nonempty.assign((size_t)n, 0);
     for (int64_t b0 = 0; b0 < g.L[0]; ++b0)
         for (int64_t b1 = 0; b1 < g.L[1]; ++b1)
-            for (int64_t b2 = 0; b2 < g.L[2]; ++b2) g.nonempty[(size_t)g.id(b0, b1, b2)] = tile_nonempty(g, b0, b1, b2);
+            for (int64_t b2 = 0; b2 < g.L[2]; ++b2) g.nonempty[(size_t)g.id(b0, b1, b2)] = nonempty(b0, b1, b2);
     g.prefix.assign((size_t)(g.L[0] + 1) * (g.L[1] + 1) * (g.L[2] + 1), 0);
     for (int64_t b0 = 1; b0 <= g.L[0]; ++b0)
         for (int64_t b1 = 1; b1 <= g.L[1]; ++b1)
@@ -147,6 +153,48 @@ void recurse(const GsLattice& g, const int32_t* theta, const int64_t* lo, const 
     }
 }
 
+// Queue (wavefront or recursive order) and per-tile dependency counts (the
+// non-empty tiles among the seven lower neighbours) of a built lattice.
+void order_and_deps(const GsLattice& g, int recursive, const int32_t* theta, std::vector<int32_t>& queue,
+                    std::vector<int32_t>& deps) {
+    queue.clear();
+    if (recursive) {
+        int64_t lo[3] = {0, 0, 0}, size[3];
+        for (int d = 0; d < 3; ++d) {
+            int64_t w = theta[d];
+            while (w < g.L[d]) w *= 2;
+            size[d] = w;
+        }
+        recurse(g, theta, lo, size, queue);
+    } else {
+        const int64_t lo[3] = {0, 0, 0}, size[3] = {g.L[0], g.L[1], g.L[2]};
+        emit_wavefront(g, lo, size, queue);
+    }
+    const int64_t n = (int64_t)g.L[0] * g.L[1] * g.L[2];
+    deps.assign((size_t)n, 0);
+    for (int64_t b0 = 0; b0 < g.L[0]; ++b0)
+        for (int64_t b1 = 0; b1 < g.L[1]; ++b1)
+            for (int64_t b2 = 0; b2 < g.L[2]; ++b2) {
+                if (!g.nonempty[(size_t)g.id(b0, b1, b2)]) continue;
+                int c = 0;
+                for (int m = 1; m < 8; ++m) {
+                    const int64_t p0 = b0 - ((m >> 2) & 1), p1 = b1 - ((m >> 1) & 1), p2 = b2 - (m & 1);
+                    if (p0 < 0 || p1 < 0 || p2 < 0) continue;
+                    if (g.nonempty[(size_t)g.id(p0, p1, p2)]) ++c;
+                }
+                deps[(size_t)g.id(b0, b1, b2)] = c;
+            }
+}
+
+bool lattice_too_big(const int64_t* ext, const int32_t* tile) {
+    int64_t cells = 1;
+    for (int d = 0; d < 3; ++d) {
+        cells *= (ext[d] + tile[d] - 1) / tile[d];
+        if (cells > (int64_t)1 << 28) return true;
+    }
+    return false;
+}
+
 }  // namespace
 
 bool gs_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
@@ -163,39 +211,43 @@ bool gs_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursi
     g.T = T;
     for (int d = 0; d < 3; ++d) g.tile[d] = tile[d];
     const int64_t ext[3] = {T, T - 1 + n0, 2 * T - 3 + n0 + n1};
-    int64_t cells = 1;
-    for (int d = 0; d < 3; ++d) {
-        cells *= (ext[d] + tile[d] - 1) / tile[d];
-        if (cells > (int64_t)1 << 28) return false;
-    }
-    build_lattice(g);
-    out->queue.clear();
-    if (recursive) {
-        int64_t lo[3] = {0, 0, 0}, size[3];
-        for (int d = 0; d < 3; ++d) {
-            int64_t w = theta[d];
-            while (w < g.L[d]) w *= 2;
-            size[d] = w;
-        }
-        recurse(g, theta, lo, size, out->queue);
-    } else {
-        const int64_t lo[3] = {0, 0, 0}, size[3] = {g.L[0], g.L[1], g.L[2]};
-        emit_wavefront(g, lo, size, out->queue);
-    }
-    const int64_t n = (int64_t)g.L[0] * g.L[1] * g.L[2];
-    out->deps.assign((size_t)n, 0);
-    for (int64_t b0 = 0; b0 < g.L[0]; ++b0)
-        for (int64_t b1 = 0; b1 < g.L[1]; ++b1)
-            for (int64_t b2 = 0; b2 < g.L[2]; ++b2) {
-                if (!g.nonempty[(size_t)g.id(b0, b1, b2)]) continue;
-                int c = 0;
-                for (int m = 1; m < 8; ++m) {
-                    const int64_t p0 = b0 - ((m >> 2) & 1), p1 = b1 - ((m >> 1) & 1), p2 = b2 - (m & 1);
-                    if (p0 < 0 || p1 < 0 || p2 < 0) continue;
-                    if (g.nonempty[(size_t)g.id(p0, p1, p2)]) ++c;
-                }
-                out->deps[(size_t)g.id(b0, b1, b2)] = c;
-            }
+    if (lattice_too_big(ext, tile)) return false;
+    build_lattice(g, ext, [&](int64_t b0, int64_t b1, int64_t b2) { return tile_nonempty(g, b0, b1, b2); });
+    order_and_deps(g, recursive, theta, out->queue, out->deps);
+    for (int d = 0; d < 3; ++d) out->lattice[d] = g.L[d];
+    return true;
+}
+
+bool skew_plan(int64_t n0, int64_t n1, int64_t T, const int32_t* tile, int recursive, const int32_t* theta,
+               GsPlanHost* out) {
+    if (n0 < 1 || n1 < 1 || T < 1 || !tile || !out) return false;
+    // Dependences move at most 1 in t and at most 2 in a and c, so tiles at
+    // least 1 x 2 x 2 wide cross at most one tile boundary per axis.
+    if (tile[0] < 1 || tile[1] < 2 || tile[2] < 2) return false;
+    for (int d = 0; d < 3; ++d)
+        if (recursive && (!theta || theta[d] < 1)) return false;
+    GsLattice g;
+    g.n0 = n0;
+    g.n1 = n1;
+    g.T = T;
+    for (int d = 0; d < 3; ++d) g.tile[d] = tile[d];
+    // (t, a, c) = (t, t + i, t + j): 0 <= t < T, 1 <= i <= n0, 1 <= j <= n1;
+    // a and c start at 1
+    const int64_t ext[3] = {T, T - 1 + n0, T - 1 + n1};
+    if (lattice_too_big(ext, tile)) return false;
+    // Exact emptiness: the steps t at which the tile's a-range meets
+    // [t + 1, t + n0] form the interval [a_lo - n0, a_hi - 1]; likewise for
+    // c; the tile holds a point iff these intervals, the tile's steps and
+    // [0, T) share a step.
+    build_lattice(g, ext, [&](int64_t b0, int64_t b1, int64_t b2) {
+        const int64_t t_lo = b0 * tile[0], t_hi = std::min<int64_t>(t_lo + tile[0], T) - 1;
+        const int64_t a_lo = 1 + b1 * tile[1], a_hi = a_lo + tile[1] - 1;
+        const int64_t c_lo = 1 + b2 * tile[2], c_hi = c_lo + tile[2] - 1;
+        const int64_t lo = std::max({t_lo, a_lo - n0, c_lo - n1, (int64_t)0});
+        const int64_t hi = std::min({t_hi, a_hi - 1, c_hi - 1});
+        return lo <= hi;
+    });
+    order_and_deps(g, recursive, theta, out->queue, out->deps);
     for (int d = 0; d < 3; ++d) out->lattice[d] = g.L[d];
     return true;
 }

@@ -86,7 +86,7 @@ FP32_RUNS = [
     ("cot-l2-leaves", "cot", dict(tile=(32, 112), time_depth=8, cot_threshold=(8, 8, 8))),
     ("sweep", "sweep", None),
 ]
-SCHED = {"sweep": pcot.PCOT_SWEEP, "slt": pcot.PCOT_SLT, "cot": pcot.PCOT_COT}
+SCHED = {"sweep": pcot.PCOT_SWEEP, "slt": pcot.PCOT_SLT, "cot": pcot.PCOT_COT, "skew": pcot.PCOT_SKEW}
 
 
 @pytest.mark.parametrize("name,sched,prm", FP32_RUNS, ids=[r[0] for r in FP32_RUNS])
@@ -107,6 +107,8 @@ FP64_RUNS = [
     ("slt-k4", "slt", dict(tile=(64, 56), time_depth=4)),
     ("cot-k4", "cot", dict(tile=(64, 56), time_depth=4, cot_threshold=(2, 256, 256))),
     ("sweep", "sweep", None),
+    ("skew-k4", "skew", dict(tile=(32, 64), time_depth=4)),
+    ("slt-k1", "slt", dict(tile=(64, 0), time_depth=1)),
 ]
 
 
@@ -123,7 +125,8 @@ def test_heat2d_8192_fp64_exact_bitwise(heat2d_full, name, sched, prm):
     pcot.pcot_destroy(h)
 
 
-@pytest.mark.parametrize("name,sched,prm", [FP64_RUNS[2], FP64_RUNS[3]], ids=["cot-k4", "sweep"])
+@pytest.mark.parametrize("name,sched,prm", [FP64_RUNS[2], FP64_RUNS[3], FP64_RUNS[4]],
+                         ids=["cot-k4", "sweep", "skew-k4"])
 def test_heat2d_8192_fp64_fma_mode(heat2d_full, name, sched, prm):
     """PCOT_F64 (FMA) against the FP64 oracle: within the rounding bound of
     five roundings per term and step on each side (positive fields)."""
