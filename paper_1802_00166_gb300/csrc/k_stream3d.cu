@@ -121,35 +121,49 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
     const bool warp_xint = __all_sync(kFull, lane_xint);
     const bool brick_ok = per || (brick_int && warp_xint);  // no pass-through inside this brick
 
-    // Offsets inside a plane (computed once per tile): of the brick's rows,
-    // of this lane's first loaded cell in each row, of its first stored cell.
-    int64_t yoff[RY], loff[RY], soff[RY];
+    // Offsets inside a plane (computed once per tile, 32-bit: choose() admits
+    // planes of fewer than 2^30 cells): of the brick's rows, of this lane's
+    // first loaded cell in each row, of its first stored cell.
+    int32_t yoff[RY], loff[RY], soff[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-        yoff[r] = ysrc[r] * Py;
-        loff[r] = yoff[r] + col[0];
-        soff[r] = (ybase + r) * Py + xl;
+        yoff[r] = (int32_t)(ysrc[r] * Py);
+        loff[r] = yoff[r] + (int32_t)col[0];
+        soff[r] = (int32_t)((ybase + r) * Py + xl);
     }
 
-    // The brick's rows of input plane zi (plane index and bounds once per
-    // plane).  Per row a lane loads its two cells as one vector (lfast) or,
-    // next to a wrap-around or the grid's edge and on unaligned layouts, cell
-    // by cell (lslow) -- decided once per tile.
+    // The brick's rows of one input plane (its offset and bounds tracked
+    // incrementally, one plane per z-step).  Per row a lane loads its two
+    // cells as one vector (lfast) or, next to a wrap-around or the grid's
+    // edge and on unaligned layouts, cell by cell (lslow) -- decided once per
+    // tile.
     bool lfast[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) lfast[r] = yin[r] && lvec;
     const bool lslow = !lvec;
-    auto load_plane = [&](int64_t zi, T (&v)[RY][E]) {
-        int64_t zs;
-        bool zin;
-        if (per) {
-            zs = wrap_fast(zi, nz);
-            zin = true;
+    bool rows_fast = true;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) rows_fast = rows_fast && lfast[r];
+    const bool warp_lfast = __all_sync(kFull, rows_fast);  // every row of every lane: one vector load
+    int64_t lz = per ? wrap_fast(z0 - K, nz) : z0 - K;  // storage index of the plane loaded next
+    int64_t lofs = lz * Pz;
+    auto load_plane = [&](T (&v)[RY][E]) {
+        const bool zin = per || (lz >= 0 && lz < ez);
+        const T* plane = src + lofs;
+        if (zin && warp_lfast) {
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const V q = gload<CG>(reinterpret_cast<const V*>(plane + loff[r]));
+                v[r][0] = q.x;
+                v[r][1] = q.y;
+            }
+            // plane lz + 2 into L2 ahead of its load (skipped at a wrap or the grid's end)
+            if (lz + 2 < (per ? nz : ez)) {
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(plane + 2 * Pz + loff[r]));
+            }
         } else {
-            zs = zi;
-            zin = zi >= 0 && zi < ez;
-        }
-        const T* plane = src + zs * Pz;
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             if (zin && lfast[r]) {
@@ -166,15 +180,30 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             for (int r = 0; r < RY; ++r)
 #pragma unroll
                 for (int j = 0; j < E; ++j)
-                    if (zin && yin[r] && inb[j]) v[r][j] = gload<CG>(plane + yoff[r] + col[j]);
+                    if (zin && yin[r] && inb[j]) v[r][j] = gload<CG>(plane + yoff[r] + (int32_t)col[j]);
+        }
+        }
+        if (per && lz + 1 == nz) {
+            lz = 0;
+            lofs = 0;
+        } else {
+            ++lz;
+            lofs += Pz;
         }
     };
 
-    // sm[buf][s][w][edge][32*E]: edge 0 = the brick's first row, 1 = its last.
+    // sm[buf][w][s][edge][32*E]: edge 0 = the brick's first row, 1 = its last.
+    // A warp's slots sit at a compile-time stride, so its neighbours' slots
+    // are at fixed offsets from its own.
     constexpr int rowlen = 32 * E;
-    const int warp_stride = 2 * rowlen;
-    const int stage_stride = NW * warp_stride;
-    const int buf_stride = K * stage_stride;
+    constexpr int WS = K * 2 * rowlen;  // one warp's slots of one buffer
+    T* const my0 = sm + w * WS + lane * E;
+    T* const my1 = my0 + NW * WS;
+    // The first and last warps read their own slots in place of a missing
+    // neighbour's: those rows are the tile's halo, whose values never reach
+    // a stored cell within K steps, so no per-stage select is needed.
+    const int up_off = w > 0 ? -WS : 0;
+    const int dn_off = w < NW - 1 ? WS : 0;
 
     T R[K][3][RY][E];
 #pragma unroll
@@ -186,7 +215,10 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
 #pragma unroll
                 for (int j = 0; j < E; ++j) R[s][u][r][j] = T(0);
 
-    const int64_t zbeg = z0 - K, zend = z0 + Hz + K;
+    // The planes z0-K .. z0+Hz+K-1 stream through, rounded up to whole
+    // iterations of the 3-step loop below (the extra planes are computed and
+    // not stored), so every iteration runs all three steps unconditionally.
+    const int64_t zbeg = z0 - K, zend = zbeg + (Hz + 2 * K + 2) / 3 * 3;
     // Stores: plane zi - K is written for zi in [zs_lo, zs_hi) (the tile's
     // planes inside the grid's interior); per row, a lane either stores its
     // two cells as one vector (sfast) or, on a ragged or unaligned edge, cell
@@ -205,20 +237,16 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
 #pragma unroll
     for (int r = 0; r < RY; ++r) sfast[r] = ystore[r] && svec;
     const bool sslow = !svec && any_stx;
-    T pf[RY][E];
-    load_plane(zbeg, pf);
+    int64_t sofs = (zbeg - K) * Pz;  // offset of plane zi - K, advanced one plane per z-step
+    load_plane(R[0][2]);  // the first plane: stage 0's newest plane of step 0
     int buf = 0;
 
     auto step = [&](auto Uc, int64_t zi) {
         constexpr int U = decltype(Uc)::value;
         constexpr int SA = U % 3, SB = (U + 1) % 3, SN = (U + 2) % 3;
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            R[0][SN][r][0] = pf[r][0];
-            R[0][SN][r][1] = pf[r][1];
-        }
-        if (zi + 1 < zend) load_plane(zi + 1, pf);
-        T* smb = sm + buf * buf_stride;
+        T* const mine = buf ? my1 : my0;
+        const T* const up = mine + up_off;
+        const T* const dn = mine + dn_off;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             V q0, q1;
@@ -226,21 +254,17 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             q0.y = R[s][SB][0][1];
             q1.x = R[s][SB][RY - 1][0];
             q1.y = R[s][SB][RY - 1][1];
-            T* wp = smb + s * stage_stride + w * warp_stride + lane * E;
-            *reinterpret_cast<V*>(wp) = q0;
-            *reinterpret_cast<V*>(wp + rowlen) = q1;
+            *reinterpret_cast<V*>(mine + s * 2 * rowlen) = q0;
+            *reinterpret_cast<V*>(mine + s * 2 * rowlen + rowlen) = q1;
         }
         __syncthreads();
         T out[RY][E];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             const int64_t zr = zi - s - 1;  // plane of time level s+1 produced now
-            const T* sp = smb + s * stage_stride + lane * E;
-            V nq, sq;  // row above the brick, row below the brick
-            if (w > 0) nq = *reinterpret_cast<const V*>(sp + (w - 1) * warp_stride + rowlen);
-            else { nq.x = R[s][SB][0][0]; nq.y = R[s][SB][0][1]; }
-            if (w < NW - 1) sq = *reinterpret_cast<const V*>(sp + (w + 1) * warp_stride);
-            else { sq.x = R[s][SB][RY - 1][0]; sq.y = R[s][SB][RY - 1][1]; }
+            // row above the brick, row below the brick
+            const V nq = *reinterpret_cast<const V*>(up + s * 2 * rowlen + rowlen);
+            const V sq = *reinterpret_cast<const V*>(dn + s * 2 * rowlen);
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 const T n0 = r > 0 ? R[s][SB][r - 1][0] : nq.x;
@@ -294,9 +318,12 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                     R[s + 1][SN][r][1] = out[r][1];
                 }
             }
+            // stage 0 is done with its oldest plane: the next input plane,
+            // stage 0's newest in the next step, is loaded into that slot
+            if (s == 0 && zi + 1 < zend) load_plane(R[0][SA]);
         }
         if (zi >= zs_lo && zi < zs_hi) {
-            T* const plane = dst + (zi - K) * Pz;
+            T* const plane = dst + sofs;
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 if (sfast[r]) {
@@ -314,13 +341,14 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
                         if (ystore[r] && stx[j]) plane[soff[r] + j] = out[r][j];
             }
         }
+        sofs += Pz;
         buf ^= 1;
     };
 
     for (int64_t zi = zbeg; zi < zend; zi += 3) {
         step(IC<0>{}, zi);
-        if (zi + 1 < zend) step(IC<1>{}, zi + 1);
-        if (zi + 2 < zend) step(IC<2>{}, zi + 2);
+        step(IC<1>{}, zi + 1);
+        step(IC<2>{}, zi + 2);
     }
 }
 
@@ -472,6 +500,8 @@ bool choose(const LaunchCtx& L, const int32_t* req, int depth, TileGeo* t) {
     if (req && req[2] > 0 && req[2] < Wx) Wx = ((req[2] + E - 1) / E) * E;
     if (Wx > Wo) Wx = Wo;
     if (Wx < Kp) Wx = Kp;
+    // 32-bit in-plane offsets (larger planes go to the generic kernel)
+    if (L.geo.s[0] >= ((int64_t)1 << 30)) return false;
     t->family = kFamStream3D;
     t->depth = depth;
     t->nwarps = nw;
