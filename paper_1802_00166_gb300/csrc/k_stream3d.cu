@@ -165,23 +165,23 @@ __device__ __forceinline__ void cta_tile(const T* __restrict__ src, T* __restric
             }
         } else {
 #pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            if (zin && lfast[r]) {
-                const V q = gload<CG>(reinterpret_cast<const V*>(plane + loff[r]));
-                v[r][0] = q.x;
-                v[r][1] = q.y;
-            } else {
-                v[r][0] = T(0);
-                v[r][1] = T(0);
+            for (int r = 0; r < RY; ++r) {
+                if (zin && lfast[r]) {
+                    const V q = gload<CG>(reinterpret_cast<const V*>(plane + loff[r]));
+                    v[r][0] = q.x;
+                    v[r][1] = q.y;
+                } else {
+                    v[r][0] = T(0);
+                    v[r][1] = T(0);
+                }
             }
-        }
-        if (lslow) {
+            if (lslow) {
 #pragma unroll
-            for (int r = 0; r < RY; ++r)
+                for (int r = 0; r < RY; ++r)
 #pragma unroll
-                for (int j = 0; j < E; ++j)
-                    if (zin && yin[r] && inb[j]) v[r][j] = gload<CG>(plane + yoff[r] + (int32_t)col[j]);
-        }
+                    for (int j = 0; j < E; ++j)
+                        if (zin && yin[r] && inb[j]) v[r][j] = gload<CG>(plane + yoff[r] + (int32_t)col[j]);
+            }
         }
         if (per && lz + 1 == nz) {
             lz = 0;
