@@ -452,7 +452,7 @@ def run_gpu(args):
         j1, j1_out = run_jacobi1d(pcot, stream, args.steps)
         j3, j3_out = run_jacobi3d(pcot, stream, args.steps, peak)
         f64, f64_out = run_heat2d_f64(pcot, stream, args.steps, g0)
-        configs = {"jacobi1d": j1, "jacobi3d": j3, "batched": run_batched(pcot, stream, args.steps),
+        configs = {"jacobi1d": j1, "jacobi3d": j3, "batched": run_batched(pcot, stream, args.steps, peak),
                    "heat2d_f64": f64}
     if rank == 0 and not args.no_cpu_baseline:
         cpu, ref = _cpu_oracle_heat2d(g0, full=extra)
@@ -890,7 +890,7 @@ def run_la(pcot, h, stream, steps):
     return out
 
 
-def run_batched(pcot, stream, steps):
+def run_batched(pcot, stream, steps, peak):
     """256 independent Heat-2D grids (sides log-uniform in [256, 2048], T in
     [64, 1024], seeded) advanced by one persistent launch replayed from a CUDA
     graph: throughput and per-grid completion latency (p50 / p99).  The tile
@@ -939,7 +939,13 @@ def run_batched(pcot, stream, steps):
     ms = e0.elapsed_time(e1) / reps
     d = done.cpu().numpy().astype(np.float64)
     lat = (d[1:] - d[0]) / 1e6
+    # HBM roof at the picked depth k: every time block reads and writes each
+    # grid's interior once (the headline's model, summed over the grids)
+    k = int(best["time_depth"])
+    alg_bytes = sum(math.ceil(T / k) * 2.0 * side * side * 4 for side, T, _ in probs)
     return {"grids": len(probs), "updates": updates, "ms": ms, "GUpdates/s": updates / ms / 1e6,
+            "roofline": {"bound": "hbm", "alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / ms / 1e6,
+                         "peak_gbs": peak, "frac": alg_bytes / ms / 1e6 / peak},
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "latency_ms_max": float(lat.max()), "launch": "one persistent kernel, CUDA graph",
             "params": {a: list(v) if isinstance(v, tuple) else v for a, v in best.items()},
