@@ -134,7 +134,9 @@ pcot_status pcot_destroy(pcot_handle h);
  * schedule, in bytes (a twin of the grid with the same strides, plus the
  * per-run dependency counters and tile queue of PCOT_COT, which grow with the
  * number of time blocks).  `params` may be NULL (defaults).  For PCOT_AUTO:
- * the largest need over the picker's candidates (no GPU needed).
+ * the largest need over the picker's candidates (no GPU needed).  For
+ * PCOT_SKEW: the twin plus a bound on its tile queue and counters.  A
+ * schedule value outside the enum gives PCOT_ERR_INVALID_ARG.
  */
 pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t *sizes, const int64_t *strides,
                                  int64_t T, pcot_dtype dtype, pcot_schedule schedule,
@@ -339,6 +341,9 @@ pcot_status pcot_mlp_argmin(const float *y, int n, int stride, int col, int *out
  *  log2 tile_0, log2 tile_1, log2 tile_2 (extents actually used; the grid
  *  extents for the sweep), log2 k (0 for the sweep), log2 of the leaf
  *  orthant volume in tiles (PCOT_COT) or -1 (sweep / single-level), dtype].
+ * Defined for the picker's schedules (sweep, single-level, recursive):
+ * PCOT_AUTO and PCOT_SKEW give PCOT_ERR_UNSUPPORTED, other values
+ * PCOT_ERR_INVALID_ARG.
  */
 pcot_status pcot_features(pcot_handle h, const int64_t *sizes, int64_t T, pcot_dtype dtype,
                           pcot_schedule schedule, const pcot_tile_params *params, float *out12);

@@ -573,6 +573,7 @@ pcot_status pcot_workspace_bytes(pcot_handle h, const int64_t* sizes, const int6
                                  pcot_dtype dtype, pcot_schedule schedule, const pcot_tile_params* params,
                                  size_t* bytes) {
     if (!bytes || T < 0) return PCOT_ERR_INVALID_ARG;
+    if (schedule < PCOT_SWEEP || schedule > PCOT_SKEW) return PCOT_ERR_INVALID_ARG;
     LaunchCtx L;
     PCOT_TRY(make_ctx(h, sizes, strides, dtype, nullptr, &L));
     size_t b = twin_bytes(L);
@@ -1056,6 +1057,9 @@ float log2f_safe(double v) { return v > 0 ? (float)std::log2(v) : 0.f; }
 
 pcot_status features_impl(pcot_handle h, const int64_t* sizes, int64_t T, pcot_dtype dtype, pcot_schedule schedule,
                           const pcot_tile_params* p, float* f) {
+    // the picker's candidates are sweep, single-level and recursive tiles
+    if (schedule != PCOT_SWEEP && schedule != PCOT_SLT && schedule != PCOT_COT)
+        return schedule == PCOT_AUTO || schedule == PCOT_SKEW ? PCOT_ERR_UNSUPPORTED : PCOT_ERR_INVALID_ARG;
     LaunchCtx L;
     PCOT_TRY(make_ctx(h, sizes, nullptr, dtype, nullptr, &L));
     for (int i = 0; i < 12; ++i) f[i] = 0.f;

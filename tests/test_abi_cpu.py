@@ -198,3 +198,27 @@ def test_candidates_list_host_logic():
 def test_noalloc_limit_parsed_from_the_header():
     import paper_1802_00166_gb300 as pcot
     assert pcot.NOALLOC_MAX_BYTES == 32 * 1024 * 1024
+
+
+def test_schedule_values_outside_the_enum_are_rejected():
+    """Planning calls reject a schedule value that is not one of the enum's,
+    and the picker's feature vector is defined only for its own candidates'
+    schedules (sweep, single-level, recursive)."""
+    h = pcot.pcot_create(2, 1, [0.5, 0.125, 0.125, 0.125, 0.125], pcot.PCOT_DIRICHLET)
+    try:
+        for bad in (-1, 5, 99):
+            with pytest.raises(pcot.PcotError) as e:
+                pcot.pcot_workspace_bytes(h, (64, 64), None, 8, pcot.PCOT_F64_EXACT, bad)
+            assert e.value.status == pcot.PCOT_ERR_INVALID_ARG
+            with pytest.raises(pcot.PcotError) as e:
+                pcot.pcot_features(h, (64, 64), 8, pcot.PCOT_F32, bad)
+            assert e.value.status == pcot.PCOT_ERR_INVALID_ARG
+        for unsupported in (pcot.PCOT_AUTO, pcot.PCOT_SKEW):
+            with pytest.raises(pcot.PcotError) as e:
+                pcot.pcot_features(h, (64, 64), 8, pcot.PCOT_F32, unsupported)
+            assert e.value.status == pcot.PCOT_ERR_UNSUPPORTED
+        # the skewed schedule's workspace: the twin plus its queue bound
+        twin = pcot.pcot_workspace_bytes(h, (64, 64), None, 8, pcot.PCOT_F64_EXACT, pcot.PCOT_SWEEP)
+        assert pcot.pcot_workspace_bytes(h, (64, 64), None, 8, pcot.PCOT_F64_EXACT, pcot.PCOT_SKEW) > twin
+    finally:
+        pcot.pcot_destroy(h)
