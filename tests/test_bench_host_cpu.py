@@ -130,3 +130,23 @@ def test_energy_meter_absent_library_is_reported_not_raised():
 
     assert not bench.EnergyMeter(0, None, lib=Broken()).ok
     assert bench.energy_per_update_nj(None, lambda: None, lambda: None, 1.0) is None
+
+
+def test_fp64_configuration_names_real_schedules_and_the_dp_roof():
+    """The FP64 exact comparison in the default run names schedules the
+    library has, heads with the non-redundant skewed tiles, and states its
+    DP-pipe roof from the unit counts: 152 SMs x 2 DP instructions per clock
+    x 2.07 GHz over the 9 DP instructions (5 multiplies, 4 adds) of one
+    exact-mode update."""
+    sys.path.insert(0, ROOT)
+    import bench
+    pcot = pytest.importorskip("paper_1802_00166_gb300")
+    names = [r[0] for r in bench.F64_RUNS]
+    assert names[0] == "sweep" and bench.F64_HEAD in names
+    assert dict((r[0], r[1]) for r in bench.F64_RUNS)[bench.F64_HEAD] == "skew"
+    for _, sched, prm in bench.F64_RUNS:
+        assert sched in pcot.SCHEDULES
+        if prm is not None:
+            pcot.tile_params(**prm)
+    assert bench.F64_EXACT_INSTR_PER_UPDATE == 9
+    assert abs(bench.DP_INSTR_PER_S / bench.F64_EXACT_INSTR_PER_UPDATE / 1e9 - 69.92) < 0.01
